@@ -260,6 +260,10 @@ void gen_batch_shape(uint64_t seed, uint64_t m_lo, uint64_t m_hi, double r_lo, d
   while ((double)m > 0.25 * (double)nu * (double)nv) { nu += nu / 4 + 1; nv += nv / 4 + 1; }
   uint64_t other = nu < nv ? nu : nv;
   uint64_t dmax = other / 2 < dmax_cap ? other / 2 : dmax_cap;
+  /* the cap must leave room for m edges on both sides */
+  uint64_t need_u = (3 * m + nu - 1) / nu, need_v = (3 * m + nv - 1) / nv;
+  if (dmax < need_u) dmax = need_u;
+  if (dmax < need_v) dmax = need_v;
   if (dmax < 2) dmax = 2;
   out[0] = m; out[1] = nu; out[2] = nv; out[3] = nplant; out[4] = dmax;
   *gamma = g;

@@ -1,0 +1,140 @@
+/*
+ * pbng.h -- C ABI of the GB300 (sm_103a) butterfly counting and two-phase
+ * bipartite peeling library (tip and wing decomposition).
+ *
+ * Method: "Parallel Peeling of Bipartite Networks for Hierarchical Dense
+ * Subgraph Discovery" (Lakhotia, Kannan, Prasanna).  Every entry point cites
+ * the passage that defines the operation it performs.
+ *
+ * Conventions shared by every call
+ *  - A bipartite graph G(W=(U,V),E) is passed as its U-side CSR: u_off has
+ *    nu+1 offsets (u_off[0]=0, u_off[nu]=m, non-decreasing), u_adj has m
+ *    neighbour ids in [0,nv), each row strictly increasing (sorted, no
+ *    duplicate edges).  The edge id of an edge is its position in u_adj.
+ *    Limits: nu+nv < 2^31, m < 2^31.
+ *  - Pointers are DEVICE pointers (caller-owned; e.g. torch CUDA tensors)
+ *    unless opts->mem == PBNG_MEM_HOST, in which case graph and output
+ *    pointers are host pointers and the library copies them to and from
+ *    the device inside the call.
+ *  - Scratch memory is allocated by the library from a stream-ordered
+ *    pool on the current device and released before the call returns;
+ *    caller memory is never freed or retained.
+ *  - Work is issued on opts->stream (a cudaStream_t; NULL = legacy default
+ *    stream).  Calls synchronise that stream before returning, so that
+ *    device-side errors are reported by the return value.
+ *  - Every call returns PBNG_OK (0) or a negative PBNG_E* status; on error
+ *    the contents of output buffers are unspecified.  pbng_strerror() names
+ *    a status; pbng_last_error_detail() gives a one-line detail of the last
+ *    failure on the calling thread.
+ *  - Counts, tip numbers and wing numbers are exact uint64 integers.
+ */
+#ifndef PBNG_H
+#define PBNG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PBNG_OK 0
+#define PBNG_EINVAL (-1)    /* invalid argument or malformed CSR */
+#define PBNG_ENOMEM (-2)    /* device allocation failed */
+#define PBNG_ECUDA (-3)     /* CUDA runtime error */
+#define PBNG_ETIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define PBNG_EOVERFLOW (-5) /* a count could exceed 2^64-1 */
+#define PBNG_EBOUNDS (-6)   /* explicit partition bounds not strictly increasing */
+
+typedef struct pbng_bigraph {
+  uint32_t nu, nv;       /* |U|, |V| */
+  uint64_t m;            /* |E| */
+  const uint64_t *u_off; /* nu+1 offsets */
+  const uint32_t *u_adj; /* m neighbour ids in [0,nv), rows strictly increasing */
+} pbng_bigraph;
+
+typedef enum { PBNG_SIDE_U = 0, PBNG_SIDE_V = 1 } pbng_side;
+
+enum {
+  PBNG_BOUNDS_ESTIMATOR = 0, /* find_range with adaptive targets (Sec. 3.1.3) */
+  PBNG_BOUNDS_EXPLICIT = 2   /* caller-supplied bounds (e.g. from a learned proposer) */
+};
+enum { PBNG_MEM_DEVICE = 0, PBNG_MEM_HOST = 1 };
+
+typedef struct pbng_opts {
+  int bounds_mode;         /* PBNG_BOUNDS_*; default ESTIMATOR */
+  const uint64_t *bounds;  /* EXPLICIT: host array of n_bounds strictly increasing upper
+                              bounds theta(2..), one per coarse partition; a bound that would
+                              peel nothing falls back to the estimator */
+  uint32_t n_bounds;
+  int recount;             /* 1 (default): batch re-count when cheaper than peeling (Sec. 5.1) */
+  int compact;             /* 1 (default): dynamic graph updates (Sec. 5.2) */
+  int mem;                 /* PBNG_MEM_DEVICE (default) or PBNG_MEM_HOST */
+  int graph_rounds;        /* 1: coarse-phase rounds run as a captured CUDA graph with a
+                              device-side loop (no host round trip per round); default 0 */
+  uint64_t timeout_ns;     /* limit for bounded device waits; 0 = 10 s */
+  void *stream;            /* cudaStream_t */
+} pbng_opts;
+
+typedef struct pbng_stats {
+  uint64_t wedges_count;   /* wedges traversed by the initial count (Alg. 1) */
+  uint64_t wedges_cd;      /* wedges traversed by coarse-phase peeling + re-counts */
+  uint64_t wedges_fd;      /* wedges traversed by fine-phase peeling */
+  uint64_t updates;        /* support updates applied (atomic decrements) */
+  uint64_t links;          /* BE-Index links (wing) */
+  uint64_t blooms;         /* BE-Index blooms (wing) */
+  uint64_t rounds;         /* coarse-phase peeling iterations (rho) */
+  uint64_t recounts;       /* rounds that re-counted instead of peeling */
+  uint64_t fd_steps;       /* fine-phase peeling steps summed over partitions */
+  uint64_t wedge_bound;    /* wedge bound of counting, sum over edges of min(d_u, d_v) */
+  uint64_t ns_setup, ns_count, ns_cd, ns_part, ns_fd, ns_total;
+  uint32_t parts_used;     /* non-empty coarse partitions */
+  uint32_t reserved;
+} pbng_stats;
+
+/* Fill *o with the defaults listed above. */
+void pbng_opts_init(pbng_opts *o);
+
+/* Per-vertex and per-edge butterfly counts (Sec. 2.1, Alg. 1 "pveBcnt"):
+ * out_u[u] = butterflies containing u (nu entries), out_v[v] likewise (nv
+ * entries), out_e[e] = butterflies containing edge e (m entries, edge-id
+ * order).  Any output may be NULL to skip it.  Vertex-priority wedge
+ * traversal: vertices relabelled by decreasing degree, each wedge
+ * start-mid-last expanded only when last has the highest priority. */
+int pbng_count(const pbng_bigraph *g, uint64_t *out_u, uint64_t *out_v, uint64_t *out_e,
+               const pbng_opts *opts, pbng_stats *stats);
+
+/* Tip decomposition of one vertex side (Sec. 2.2 Def. 2 and the tip number
+ * theta_u; two-phase PBNG of Sec. 3.1 adapted to tips, Sec. 3.2): out_tip[x]
+ * = tip number of vertex x of the peeled side (nu entries for PBNG_SIDE_U,
+ * nv for PBNG_SIDE_V).  P = number of coarse partitions (P >= 1; the paper
+ * uses 150).  The result does not depend on P or on the bounds. */
+int pbng_tip_decompose(const pbng_bigraph *g, pbng_side side, uint32_t P, uint64_t *out_tip,
+                       const pbng_opts *opts, pbng_stats *stats);
+
+/* Wing decomposition (Sec. 2.2 Def. 1 and the wing number theta_e; PBNG
+ * with the BE-Index, Sec. 2.3, 3.3, Alg. 4-6): out_wing[e] = wing number of
+ * edge e (m entries, edge-id order).  P >= 1 coarse partitions. */
+int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, const pbng_opts *opts,
+                        pbng_stats *stats);
+
+/* Tip decomposition of n independent graphs in one pass: the graphs are
+ * peeled together as their disjoint union (butterflies never cross graphs,
+ * so each graph's tip numbers are those of its own decomposition, Sec. 2.2),
+ * sharing every launch, coarse round and fine-phase work queue.  outs[i]
+ * receives the tip numbers of graph i's peeled side.  With PBNG_MEM_DEVICE
+ * every gs[i] pointer and outs[i] is a device pointer; gs and outs
+ * themselves are host arrays. */
+int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng_side side, uint32_t P,
+                             uint64_t *const *outs, const pbng_opts *opts, pbng_stats *stats);
+
+/* Name of a status code. */
+const char *pbng_strerror(int status);
+/* Detail of the most recent failure on this thread ("" if none). */
+const char *pbng_last_error_detail(void);
+/* Library version, major*10000 + minor*100 + patch. */
+int pbng_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBNG_H */

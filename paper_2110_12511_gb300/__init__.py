@@ -1,0 +1,243 @@
+"""Python binding of libpbng.so: GB300 butterfly counting and two-phase
+tip / wing decomposition (Lakhotia, Kannan, Prasanna, "Parallel Peeling of
+Bipartite Networks for Hierarchical Dense Subgraph Discovery").
+
+This module only marshals arguments: every step of counting and peeling runs
+in the library's CUDA kernels.  PyTorch provides device memory and streams.
+Graphs are U-side CSRs (``u_off`` uint64[nu+1], ``u_adj`` uint32[m], rows
+sorted, no duplicates); results are uint64, returned as int64 torch tensors
+holding the same bits (use ``as_u64`` for a numpy uint64 view).
+
+If the compiled library is missing every call raises: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpbng.so")
+
+PBNG_OK, PBNG_EINVAL, PBNG_ENOMEM, PBNG_ECUDA, PBNG_ETIMEOUT, PBNG_EOVERFLOW, PBNG_EBOUNDS = 0, -1, -2, -3, -4, -5, -6
+SIDE_U, SIDE_V = 0, 1
+BOUNDS_ESTIMATOR, BOUNDS_EXPLICIT = 0, 2
+MEM_DEVICE, MEM_HOST = 0, 1
+
+
+class Bigraph(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_uint32), ("nv", ctypes.c_uint32), ("m", ctypes.c_uint64),
+                ("u_off", ctypes.c_void_p), ("u_adj", ctypes.c_void_p)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("bounds_mode", ctypes.c_int), ("bounds", ctypes.c_void_p), ("n_bounds", ctypes.c_uint32),
+                ("recount", ctypes.c_int), ("compact", ctypes.c_int), ("mem", ctypes.c_int),
+                ("graph_rounds", ctypes.c_int), ("timeout_ns", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "wedges_count", "wedges_cd", "wedges_fd", "updates", "links", "blooms", "rounds", "recounts", "fd_steps",
+        "wedge_bound", "ns_setup", "ns_count", "ns_cd", "ns_part", "ns_fd", "ns_total")] + [
+        ("parts_used", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def to_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
+
+
+class PbngError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = _lib_or_none()
+        name = lib.pbng_strerror(code).decode() if lib else str(code)
+        detail = lib.pbng_last_error_detail().decode() if lib else ""
+        super().__init__(f"{where}: {name} ({code}){': ' + detail if detail else ''}")
+        self.code = code
+
+
+_lib = None
+
+
+def _lib_or_none():
+    return _lib
+
+
+def lib():
+    """Load libpbng.so (built in-tree by ``paper_2110_12511_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_2110_12511_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, C = ctypes.c_void_p, ctypes.c_int
+        G, O, S = ctypes.POINTER(Bigraph), ctypes.POINTER(Opts), ctypes.POINTER(Stats)
+        L.pbng_opts_init.argtypes = [O]
+        L.pbng_opts_init.restype = None
+        L.pbng_count.argtypes = [G, P, P, P, O, S]
+        L.pbng_count.restype = C
+        L.pbng_tip_decompose.argtypes = [G, C, ctypes.c_uint32, P, O, S]
+        L.pbng_tip_decompose.restype = C
+        L.pbng_wing_decompose.argtypes = [G, ctypes.c_uint32, P, O, S]
+        L.pbng_wing_decompose.restype = C
+        L.pbng_tip_decompose_batch.argtypes = [G, ctypes.c_uint32, C, ctypes.c_uint32, ctypes.POINTER(P), O, S]
+        L.pbng_tip_decompose_batch.restype = C
+        L.pbng_strerror.argtypes = [C]
+        L.pbng_strerror.restype = ctypes.c_char_p
+        L.pbng_last_error_detail.argtypes = []
+        L.pbng_last_error_detail.restype = ctypes.c_char_p
+        L.pbng_version.argtypes = []
+        L.pbng_version.restype = C
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != PBNG_OK:
+        raise PbngError(rc, where)
+
+
+def as_u64(t) -> np.ndarray:
+    """numpy uint64 view of a result tensor (int64 storage of uint64 bits)."""
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+@dataclass
+class DeviceGraph:
+    """A bipartite graph resident on the GPU (torch tensors)."""
+    nu: int
+    nv: int
+    u_off: "object"  # torch int64 tensor holding uint64 offsets
+    u_adj: "object"  # torch int32 tensor holding uint32 ids
+
+    @property
+    def m(self) -> int:
+        return int(self.u_adj.numel())
+
+    def c_struct(self) -> Bigraph:
+        return Bigraph(self.nu, self.nv, self.m, self.u_off.data_ptr(), self.u_adj.data_ptr() if self.m else 0)
+
+
+def to_device(g, device="cuda") -> DeviceGraph:
+    """Copy a host graph (``bigraph_gen.Graph`` or anything with nu, nv,
+    u_off, u_adj numpy arrays) to the GPU."""
+    import torch
+    off = torch.from_numpy(np.ascontiguousarray(g.u_off, dtype=np.uint64).view(np.int64)).to(device)
+    adj = torch.from_numpy(np.ascontiguousarray(g.u_adj, dtype=np.uint32).view(np.int32)).to(device)
+    return DeviceGraph(int(g.nu), int(g.nv), off, adj)
+
+
+def _opts(stream=None, bounds=None, recount=True, compact=True, mem=MEM_DEVICE, graph_rounds=False, keep=None):
+    o = Opts()
+    lib().pbng_opts_init(ctypes.byref(o))
+    o.recount = int(bool(recount))
+    o.compact = int(bool(compact))
+    o.mem = mem
+    o.graph_rounds = int(bool(graph_rounds))
+    if stream is not None:
+        o.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    else:
+        try:
+            import torch
+            o.stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            o.stream = None
+    if bounds is not None:
+        b = np.ascontiguousarray(bounds, dtype=np.uint64)
+        if keep is not None:
+            keep.append(b)
+        o.bounds_mode = BOUNDS_EXPLICIT
+        o.bounds = b.ctypes.data_as(ctypes.c_void_p)
+        o.n_bounds = b.size
+    return o
+
+
+def count(dg: DeviceGraph, vertices=True, edges=False, stream=None, with_stats=False):
+    """Per-vertex (U and V) and per-edge butterfly counts (Alg. 1)."""
+    import torch
+    dev = dg.u_off.device
+    cu = torch.empty(max(dg.nu, 1), dtype=torch.int64, device=dev) if vertices else None
+    cv = torch.empty(max(dg.nv, 1), dtype=torch.int64, device=dev) if vertices else None
+    ce = torch.empty(max(dg.m, 1), dtype=torch.int64, device=dev) if edges else None
+    st = Stats()
+    o = _opts(stream)
+    g = dg.c_struct()
+    rc = lib().pbng_count(ctypes.byref(g), cu.data_ptr() if cu is not None else None,
+                          cv.data_ptr() if cv is not None else None, ce.data_ptr() if ce is not None else None,
+                          ctypes.byref(o), ctypes.byref(st))
+    _check(rc, "pbng_count")
+    out = (cu[:dg.nu] if cu is not None else None, cv[:dg.nv] if cv is not None else None,
+           ce[:dg.m] if ce is not None else None)
+    return (out, st.to_dict()) if with_stats else out
+
+
+def _side(side) -> int:
+    if side in ("U", "u", 0, SIDE_U):
+        return SIDE_U
+    if side in ("V", "v", 1, SIDE_V):
+        return SIDE_V
+    raise ValueError(side)
+
+
+def tip_decompose(dg: DeviceGraph, side="U", P=150, bounds=None, recount=True, compact=True, graph_rounds=False,
+                  stream=None, with_stats=False):
+    """Tip numbers of one side (two-phase PBNG, Sec. 3.1-3.2)."""
+    import torch
+    s = _side(side)
+    n = dg.nu if s == SIDE_U else dg.nv
+    out = torch.empty(max(n, 1), dtype=torch.int64, device=dg.u_off.device)
+    keep = []
+    o = _opts(stream, bounds, recount, compact, graph_rounds=graph_rounds, keep=keep)
+    st = Stats()
+    g = dg.c_struct()
+    rc = lib().pbng_tip_decompose(ctypes.byref(g), s, int(P), out.data_ptr(), ctypes.byref(o), ctypes.byref(st))
+    _check(rc, "pbng_tip_decompose")
+    return (out[:n], st.to_dict()) if with_stats else out[:n]
+
+
+def tip_decompose_host(g, side="U", P=150, with_stats=False, **kw):
+    """Tip numbers with host input and output buffers (the library copies)."""
+    s = _side(side)
+    off = np.ascontiguousarray(g.u_off, dtype=np.uint64)
+    adj = np.ascontiguousarray(g.u_adj, dtype=np.uint32)
+    n = g.nu if s == SIDE_U else g.nv
+    out = np.zeros(max(n, 1), dtype=np.uint64)
+    o = _opts(kw.get("stream"), kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), mem=MEM_HOST,
+              keep=[])
+    st = Stats()
+    cg = Bigraph(int(g.nu), int(g.nv), adj.size, off.ctypes.data, adj.ctypes.data if adj.size else 0)
+    rc = lib().pbng_tip_decompose(ctypes.byref(cg), s, int(P), out.ctypes.data, ctypes.byref(o), ctypes.byref(st))
+    _check(rc, "pbng_tip_decompose")
+    return (out[:n], st.to_dict()) if with_stats else out[:n]
+
+
+def wing_decompose(dg: DeviceGraph, P=400, bounds=None, recount=True, compact=True, stream=None, with_stats=False):
+    """Wing numbers of every edge (BE-Index PBNG, Sec. 3.3)."""
+    import torch
+    out = torch.empty(max(dg.m, 1), dtype=torch.int64, device=dg.u_off.device)
+    keep = []
+    o = _opts(stream, bounds, recount, compact, keep=keep)
+    st = Stats()
+    g = dg.c_struct()
+    rc = lib().pbng_wing_decompose(ctypes.byref(g), int(P), out.data_ptr(), ctypes.byref(o), ctypes.byref(st))
+    _check(rc, "pbng_wing_decompose")
+    return (out[:dg.m], st.to_dict()) if with_stats else out[:dg.m]
+
+
+def tip_decompose_batch(dgs, side="U", P=150, stream=None, with_stats=False, **kw):
+    """Tip numbers of many independent graphs in one call (disjoint union)."""
+    import torch
+    s = _side(side)
+    n = len(dgs)
+    gs = (Bigraph * max(n, 1))(*[d.c_struct() for d in dgs])
+    outs = [torch.empty(max(d.nu if s == SIDE_U else d.nv, 1), dtype=torch.int64, device=d.u_off.device) for d in dgs]
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[o.data_ptr() for o in outs])
+    keep = []
+    o = _opts(stream, kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), keep=keep)
+    st = Stats()
+    rc = lib().pbng_tip_decompose_batch(gs, n, s, int(P), ptrs, ctypes.byref(o), ctypes.byref(st))
+    _check(rc, "pbng_tip_decompose_batch")
+    res = [t[:(d.nu if s == SIDE_U else d.nv)] for t, d in zip(outs, dgs)]
+    return (res, st.to_dict()) if with_stats else res

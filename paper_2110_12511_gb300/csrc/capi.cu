@@ -1,0 +1,394 @@
+// C ABI entry points (include/pbng.h): argument checks, host/device
+// marshalling, and the disjoint-union batch.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace pbng {
+extern thread_local char g_detail[512];
+
+namespace {
+
+template <class F>
+int guarded(F &&f) {
+  g_detail[0] = 0;
+  try {
+    f();
+    return PBNG_OK;
+  } catch (Error &e) {
+    return e.code;
+  } catch (std::bad_alloc &) {
+    snprintf(g_detail, sizeof(g_detail), "host allocation failed");
+    return PBNG_ENOMEM;
+  } catch (...) {
+    snprintf(g_detail, sizeof(g_detail), "unexpected internal exception");
+    return PBNG_ECUDA;
+  }
+}
+
+pbng_opts defaults() {
+  pbng_opts o;
+  pbng_opts_init(&o);
+  return o;
+}
+
+// host-side checks that need no device
+void check_graph(const pbng_bigraph *g) {
+  if (!g) fail(PBNG_EINVAL, "null graph");
+  if (!g->u_off) fail(PBNG_EINVAL, "null u_off");
+  if (g->m && !g->u_adj) fail(PBNG_EINVAL, "null u_adj with m > 0");
+  if ((uint64_t)g->nu + g->nv >= (1ull << 31) || g->m >= (1ull << 31))
+    fail(PBNG_EINVAL, "graph exceeds the size limits (nu+nv < 2^31, m < 2^31)");
+}
+
+// Device view of the caller's graph: copies host arrays when mem == HOST.
+pbng_bigraph device_graph(Arena &a, const pbng_bigraph *g, int mem) {
+  check_graph(g);
+  if (!g) fail(PBNG_EINVAL, "null graph");
+  if (!g->u_off) fail(PBNG_EINVAL, "null u_off");
+  if (g->m && !g->u_adj) fail(PBNG_EINVAL, "null u_adj with m > 0");
+  if ((uint64_t)g->nu + g->nv >= (1ull << 31) || g->m >= (1ull << 31))
+    fail(PBNG_EINVAL, "graph exceeds the size limits (nu+nv < 2^31, m < 2^31)");
+  pbng_bigraph d = *g;
+  if (mem == PBNG_MEM_HOST) {
+    uint64_t *off = a.alloc<uint64_t>((size_t)g->nu + 1);
+    CK(cudaMemcpyAsync(off, g->u_off, ((size_t)g->nu + 1) * 8, cudaMemcpyHostToDevice, a.st));
+    uint32_t *adj = a.alloc<uint32_t>(g->m ? g->m : 1);
+    if (g->m) CK(cudaMemcpyAsync(adj, g->u_adj, g->m * 4, cudaMemcpyHostToDevice, a.st));
+    d.u_off = off;
+    d.u_adj = adj;
+  }
+  return d;
+}
+
+struct OutBuf {  // device output buffer, copied back to host memory if needed
+  uint64_t *user = nullptr, *dev = nullptr;
+  size_t n = 0;
+  int mem = 0;
+  void init(Arena &a, uint64_t *p, size_t count, int m) {
+    user = p;
+    n = count;
+    mem = m;
+    if (!p) return;
+    dev = mem == PBNG_MEM_HOST ? a.alloc<uint64_t>(n ? n : 1) : p;
+  }
+  void finish(Arena &a) {
+    if (user && mem == PBNG_MEM_HOST && n) CK(cudaMemcpyAsync(user, dev, n * 8, cudaMemcpyDeviceToHost, a.st));
+  }
+};
+
+__global__ void k_gather_lab(const unsigned long long *cnt_lab, const uint32_t *g2lab, uint32_t off, uint32_t n,
+                             uint64_t *out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = cnt_lab[g2lab[off + i]];
+}
+
+TipParams tip_params(uint32_t P, const pbng_opts &o) {
+  if (P == 0) fail(PBNG_EINVAL, "P must be >= 1");
+  if (o.bounds_mode != PBNG_BOUNDS_ESTIMATOR && o.bounds_mode != PBNG_BOUNDS_EXPLICIT)
+    fail(PBNG_EINVAL, "unknown bounds_mode %d", o.bounds_mode);
+  if (o.bounds_mode == PBNG_BOUNDS_EXPLICIT) {
+    if (o.n_bounds && !o.bounds) fail(PBNG_EINVAL, "null bounds with n_bounds > 0");
+    for (uint32_t i = 1; i < o.n_bounds; i++)
+      if (o.bounds[i] <= o.bounds[i - 1]) fail(PBNG_EBOUNDS, "bounds must be strictly increasing (index %u)", i);
+  }
+  TipParams p;
+  p.P = P;
+  p.bounds_mode = o.bounds_mode;
+  p.bounds = o.bounds;
+  p.n_bounds = o.bounds_mode == PBNG_BOUNDS_EXPLICIT ? o.n_bounds : 0;
+  p.recount = o.recount;
+  p.compact = o.compact;
+  p.graph_rounds = o.graph_rounds;
+  p.timeout_ns = o.timeout_ns ? o.timeout_ns : 10000000000ull;
+  return p;
+}
+
+struct Timer {
+  cudaEvent_t a, b;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  uint64_t ns() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    return (uint64_t)(ms * 1e6);
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+}  // namespace
+}  // namespace pbng
+
+using namespace pbng;
+
+extern "C" {
+
+void pbng_opts_init(pbng_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->bounds_mode = PBNG_BOUNDS_ESTIMATOR;
+  o->recount = 1;
+  o->compact = 1;
+  o->mem = PBNG_MEM_DEVICE;
+}
+
+const char *pbng_strerror(int s) {
+  switch (s) {
+    case PBNG_OK: return "ok";
+    case PBNG_EINVAL: return "invalid argument";
+    case PBNG_ENOMEM: return "out of device memory";
+    case PBNG_ECUDA: return "CUDA error";
+    case PBNG_ETIMEOUT: return "device wait timed out";
+    case PBNG_EOVERFLOW: return "count overflow";
+    case PBNG_EBOUNDS: return "bounds not strictly increasing";
+    default: return "unknown status";
+  }
+}
+
+const char *pbng_last_error_detail(void) { return g_detail; }
+
+int pbng_version(void) { return 100; }
+
+int pbng_count(const pbng_bigraph *g, uint64_t *out_u, uint64_t *out_v, uint64_t *out_e, const pbng_opts *opts,
+               pbng_stats *stats) {
+  pbng_opts o = opts ? *opts : defaults();
+  return guarded([&] {
+    check_graph(g);
+    init_device_pool();
+    Arena a((cudaStream_t)o.stream);
+    Timer tm(a.st);
+    pbng_bigraph d = device_graph(a, g, o.mem);
+    Graph G;
+    build_graph(a, d, true, out_e != nullptr, G);
+    OutBuf bu, bv, be;
+    bu.init(a, out_u, G.nu, o.mem);
+    bv.init(a, out_v, G.nv, o.mem);
+    be.init(a, out_e, G.m, o.mem);
+    uint64_t *cnt = a.zeros<uint64_t>((size_t)G.n + 1);
+    if (be.dev && G.m) CK(cudaMemsetAsync(be.dev, 0, (size_t)G.m * 8, a.st));
+    uint64_t *wd = a.zeros<uint64_t>(1);
+    CountOut co;
+    co.cnt_lab = cnt;
+    co.cnt_e = be.dev;
+    co.wedges = wd;
+    count_butterflies(a, G, co);
+    if (bu.dev && G.nu)
+      k_gather_lab<<<grid_for(G.nu, 256, 16 * num_sms()), 256, 0, a.st>>>((unsigned long long *)cnt, G.g2lab, 0, G.nu, bu.dev);
+    if (bv.dev && G.nv)
+      k_gather_lab<<<grid_for(G.nv, 256, 16 * num_sms()), 256, 0, a.st>>>((unsigned long long *)cnt, G.g2lab, G.nu, G.nv, bv.dev);
+    CK_LAUNCH();
+    bu.finish(a);
+    bv.finish(a);
+    be.finish(a);
+    uint64_t w = fetch(a, wd);
+    CK(cudaStreamSynchronize(a.st));
+    if (stats) {
+      memset(stats, 0, sizeof(*stats));
+      stats->wedges_count = w;
+      stats->wedge_bound = G.wedge_bound;
+      stats->ns_total = tm.ns();
+    }
+  });
+}
+
+int pbng_tip_decompose(const pbng_bigraph *g, pbng_side side, uint32_t P, uint64_t *out_tip, const pbng_opts *opts,
+                       pbng_stats *stats) {
+  pbng_opts o = opts ? *opts : defaults();
+  return guarded([&] {
+    if (side != PBNG_SIDE_U && side != PBNG_SIDE_V) fail(PBNG_EINVAL, "side must be PBNG_SIDE_U or PBNG_SIDE_V");
+    if (!out_tip) fail(PBNG_EINVAL, "null out_tip");
+    TipParams p = tip_params(P, o);
+    check_graph(g);
+    init_device_pool();
+    Arena a((cudaStream_t)o.stream);
+    Timer tm(a.st);
+    pbng_bigraph d = device_graph(a, g, o.mem);
+    Graph G;
+    build_graph(a, d, true, false, G);
+    OutBuf out;
+    out.init(a, out_tip, side == PBNG_SIDE_U ? G.nu : G.nv, o.mem);
+    pbng_stats st;
+    memset(&st, 0, sizeof(st));
+    uint64_t t_setup = 0;
+    {
+      CK(cudaStreamSynchronize(a.st));
+      t_setup = tm.ns();
+    }
+    tip_decompose(a, G, side == PBNG_SIDE_U ? 0 : 1, p, out.dev, stats ? &st : nullptr);
+    out.finish(a);
+    CK(cudaStreamSynchronize(a.st));
+    if (stats) {
+      *stats = st;
+      stats->ns_setup = t_setup;
+      stats->ns_total = tm.ns();
+    }
+  });
+}
+
+int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, const pbng_opts *opts, pbng_stats *stats) {
+  pbng_opts o = opts ? *opts : defaults();
+  return guarded([&] {
+    if (!out_wing && g && g->m) fail(PBNG_EINVAL, "null out_wing");
+    TipParams p = tip_params(P, o);
+    check_graph(g);
+    init_device_pool();
+    Arena a((cudaStream_t)o.stream);
+    Timer tm(a.st);
+    pbng_bigraph d = device_graph(a, g, o.mem);
+    Graph G;
+    build_graph(a, d, true, true, G);
+    OutBuf out;
+    out.init(a, out_wing, G.m, o.mem);
+    pbng_stats st;
+    memset(&st, 0, sizeof(st));
+    CK(cudaStreamSynchronize(a.st));
+    uint64_t t_setup = tm.ns();
+    wing_decompose(a, G, p, out.dev, stats ? &st : nullptr);
+    out.finish(a);
+    CK(cudaStreamSynchronize(a.st));
+    if (stats) {
+      *stats = st;
+      stats->ns_setup = t_setup;
+      stats->ns_total = tm.ns();
+    }
+  });
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batch
+namespace pbng {
+namespace {
+struct BatchDesc {
+  const uint64_t *u_off;
+  const uint32_t *u_adj;
+  uint32_t nu, nv;
+  uint32_t m;
+  uint32_t u_base, v_base;  // offsets of this graph's vertices in the union
+  uint32_t e_base;          // offset of this graph's edges in the union
+};
+
+// one block per graph: union offsets and neighbour ids shifted into place
+__global__ void k_union(const BatchDesc *ds, uint32_t n, uint64_t *uoff, uint32_t *uadj) {
+  for (uint32_t gi = blockIdx.x; gi < n; gi += gridDim.x) {
+    BatchDesc d = ds[gi];
+    for (uint32_t u = threadIdx.x; u < d.nu; u += blockDim.x) uoff[d.u_base + u] = d.e_base + d.u_off[u];
+    for (uint32_t e = threadIdx.x; e < d.m; e += blockDim.x) uadj[d.e_base + e] = d.v_base + d.u_adj[e];
+  }
+}
+
+__global__ void k_scatter_out(const uint64_t *theta, const BatchDesc *ds, uint32_t n, uint64_t *const *outs, int side) {
+  for (uint32_t gi = blockIdx.x; gi < n; gi += gridDim.x) {
+    BatchDesc d = ds[gi];
+    uint64_t *o = outs[gi];
+    uint32_t cnt = side == 0 ? d.nu : d.nv, base = side == 0 ? d.u_base : d.v_base;
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) o[i] = theta[base + i];
+  }
+}
+}  // namespace
+}  // namespace pbng
+
+extern "C" int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng_side side, uint32_t P,
+                                        uint64_t *const *outs, const pbng_opts *opts, pbng_stats *stats) {
+  pbng_opts o = opts ? *opts : defaults();
+  return guarded([&] {
+    if (n == 0) return;
+    if (!gs || !outs) fail(PBNG_EINVAL, "null graph or output array");
+    if (side != PBNG_SIDE_U && side != PBNG_SIDE_V) fail(PBNG_EINVAL, "side must be PBNG_SIDE_U or PBNG_SIDE_V");
+    TipParams p = tip_params(P, o);
+    init_device_pool();
+    Arena a((cudaStream_t)o.stream);
+    Timer tm(a.st);
+    std::vector<BatchDesc> hd(n);
+    uint64_t nu = 0, nv = 0, m = 0;
+    for (uint32_t i = 0; i < n; i++) {
+      const pbng_bigraph &g = gs[i];
+      if (!g.u_off || (g.m && !g.u_adj) || !outs[i]) fail(PBNG_EINVAL, "graph %u: null pointer", i);
+      hd[i].nu = g.nu;
+      hd[i].nv = g.nv;
+      hd[i].m = (uint32_t)g.m;
+      hd[i].u_base = (uint32_t)nu;
+      hd[i].e_base = (uint32_t)m;
+      nu += g.nu;
+      m += g.m;
+      if (nu >= (1ull << 31) || m >= (1ull << 31)) fail(PBNG_EINVAL, "batch exceeds the size limits");
+    }
+    for (uint32_t i = 0; i < n; i++) {
+      hd[i].v_base = (uint32_t)nv;
+      nv += gs[i].nv;
+    }
+    if (nu + nv >= (1ull << 31)) fail(PBNG_EINVAL, "batch exceeds the size limits");
+    // inputs on the device (copy host graphs first)
+    for (uint32_t i = 0; i < n; i++) {
+      if (o.mem == PBNG_MEM_HOST) {
+        uint64_t *off = a.alloc<uint64_t>((size_t)gs[i].nu + 1);
+        uint32_t *adj = a.alloc<uint32_t>(gs[i].m ? gs[i].m : 1);
+        CK(cudaMemcpyAsync(off, gs[i].u_off, ((size_t)gs[i].nu + 1) * 8, cudaMemcpyHostToDevice, a.st));
+        if (gs[i].m) CK(cudaMemcpyAsync(adj, gs[i].u_adj, gs[i].m * 4, cudaMemcpyHostToDevice, a.st));
+        hd[i].u_off = off;
+        hd[i].u_adj = adj;
+      } else {
+        hd[i].u_off = gs[i].u_off;
+        hd[i].u_adj = gs[i].u_adj;
+      }
+    }
+    BatchDesc *dd = a.alloc<BatchDesc>(n);
+    CK(cudaMemcpyAsync(dd, hd.data(), n * sizeof(BatchDesc), cudaMemcpyHostToDevice, a.st));
+    uint64_t *uoff = a.alloc<uint64_t>(nu + 1);
+    uint32_t *uadj = a.alloc<uint32_t>(m ? m : 1);
+    k_union<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(dd, n, uoff, uadj);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(uoff + nu, &m, 8, cudaMemcpyHostToDevice, a.st));
+    CK(cudaStreamSynchronize(a.st));
+    pbng_bigraph ug;
+    ug.nu = (uint32_t)nu;
+    ug.nv = (uint32_t)nv;
+    ug.m = m;
+    ug.u_off = uoff;
+    ug.u_adj = uadj;
+    Graph G;
+    build_graph(a, ug, true, false, G);
+    uint32_t nx = side == PBNG_SIDE_U ? G.nu : G.nv;
+    uint64_t *theta = a.alloc<uint64_t>(nx ? nx : 1);
+    pbng_stats st;
+    memset(&st, 0, sizeof(st));
+    tip_decompose(a, G, side == PBNG_SIDE_U ? 0 : 1, p, theta, stats ? &st : nullptr);
+    // per-graph outputs
+    std::vector<uint64_t *> douts(n);
+    std::vector<uint64_t *> hbufs;
+    for (uint32_t i = 0; i < n; i++) {
+      if (o.mem == PBNG_MEM_HOST) {
+        uint32_t cnt = side == PBNG_SIDE_U ? gs[i].nu : gs[i].nv;
+        douts[i] = a.alloc<uint64_t>(cnt ? cnt : 1);
+      } else {
+        douts[i] = outs[i];
+      }
+    }
+    uint64_t **dptr = a.alloc<uint64_t *>(n);
+    CK(cudaMemcpyAsync(dptr, douts.data(), n * sizeof(uint64_t *), cudaMemcpyHostToDevice, a.st));
+    k_scatter_out<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(theta, dd, n, dptr, side == PBNG_SIDE_U ? 0 : 1);
+    CK_LAUNCH();
+    if (o.mem == PBNG_MEM_HOST)
+      for (uint32_t i = 0; i < n; i++) {
+        uint32_t cnt = side == PBNG_SIDE_U ? gs[i].nu : gs[i].nv;
+        if (cnt) CK(cudaMemcpyAsync(outs[i], douts[i], (size_t)cnt * 8, cudaMemcpyDeviceToHost, a.st));
+      }
+    CK(cudaStreamSynchronize(a.st));
+    if (stats) {
+      *stats = st;
+      stats->ns_total = tm.ns();
+    }
+  });
+}

@@ -1,0 +1,130 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "pbng.h"
+
+namespace pbng {
+
+// ------------------------------------------------------------------ errors
+struct Error {
+  int code;
+};
+[[noreturn]] void fail(int code, const char *fmt, ...);
+void cuda_check(cudaError_t e, const char *what, const char *file, int line);
+#define CK(x) ::pbng::cuda_check((x), #x, __FILE__, __LINE__)
+#define CK_LAUNCH() ::pbng::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+// -------------------------------------------------------------- allocation
+// Per-call arena of stream-ordered allocations, released when the call ends.
+struct Arena {
+  cudaStream_t st = nullptr;
+  std::vector<void *> ptrs;
+  size_t bytes = 0, peak = 0;
+  explicit Arena(cudaStream_t s) : st(s) {}
+  ~Arena();
+  void *raw(size_t nbytes);
+  template <class T>
+  T *alloc(size_t n) {
+    return static_cast<T *>(raw(n * sizeof(T)));
+  }
+  template <class T>
+  T *zeros(size_t n) {
+    T *p = alloc<T>(n);
+    CK(cudaMemsetAsync(p, 0, (n ? n : 1) * sizeof(T), st));
+    return p;
+  }
+  void free(void *p);
+};
+
+int num_sms();
+void init_device_pool();
+
+// ------------------------------------------------------------ primitives
+// out[i] = sum_{j<i} in[j] for i in [0, n]; out has n+1 entries.
+void exclusive_scan_u32(Arena &a, const uint32_t *in, uint32_t *out, size_t n);
+void exclusive_scan_u32_to_u64(Arena &a, const uint32_t *in, uint64_t *out, size_t n);
+void exclusive_scan_u64(Arena &a, const uint64_t *in, uint64_t *out, size_t n);
+// Stable LSD radix sort of (key, value) pairs on the low key_bits bits.
+// keys / vals are sorted in place (temporary buffers from the arena).
+void sort_pairs(Arena &a, uint64_t *keys, uint32_t *vals, size_t n, int key_bits);
+// device reductions to a host value (synchronises the stream)
+uint64_t reduce_sum_u64(Arena &a, const uint64_t *in, size_t n);
+uint32_t reduce_max_u32(Arena &a, const uint32_t *in, size_t n);
+// read one device value (synchronises)
+template <class T>
+T fetch(Arena &a, const T *p) {
+  T v;
+  CK(cudaMemcpyAsync(&v, p, sizeof(T), cudaMemcpyDeviceToHost, a.st));
+  CK(cudaStreamSynchronize(a.st));
+  return v;
+}
+
+static inline int bits_for(uint64_t x) {  // bits needed to represent x (>= 1)
+  int b = 1;
+  while (b < 64 && (x >> b)) b++;
+  return b;
+}
+static inline unsigned grid_for(size_t n, unsigned threads, unsigned cap = 1u << 30) {
+  size_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+// ------------------------------------------------------------------ graph
+// Internal graph in 32-bit CSR form plus the degree-priority labelled
+// adjacency used by Alg. 1.  Edge id = position in the U-side CSR.
+struct Graph {
+  uint32_t nu = 0, nv = 0, m = 0;
+  // U-side CSR (edge id = position) and V-side CSR with edge ids
+  uint32_t *u_off = nullptr, *u_adj = nullptr;
+  uint32_t *v_off = nullptr, *v_adj = nullptr, *v_eid = nullptr;
+  // labelled adjacency over W = U u V (label 0 = highest priority, Alg. 1 l.2-4)
+  uint32_t n = 0;
+  uint32_t *lab_off = nullptr, *lab_adj = nullptr, *lab_eid = nullptr;
+  uint32_t *g2lab = nullptr;  // gidx (u, or nu+v) -> label
+  uint32_t *lab2g = nullptr;  // label -> gidx
+  uint32_t maxdeg = 0;
+  uint64_t wedge_bound = 0;  // sum over edges of min(d_u, d_v)
+  bool has_labels = false;
+};
+
+// Validate a device CSR and build the internal graph.  want_labels: also
+// build the labelled adjacency (needed by counting); want_eid: keep the edge
+// ids of the labelled adjacency (per-edge counts, BE-Index).
+void build_graph(Arena &a, const pbng_bigraph &g, bool want_labels, bool want_eid, Graph &G);
+
+// -------------------------------------------------------------- counting
+struct CountOut {
+  uint64_t *cnt_lab = nullptr;   // per label (size n), accumulated (caller zeroes)
+  uint64_t *cnt_e = nullptr;     // per edge (size m) or null
+  const uint8_t *lab_alive = nullptr;  // restrict to alive labels (null = all)
+  const uint8_t *lab_isU = nullptr;    // side of each label (needed when want_side >= 0)
+  int want_side = -1;            // -1 both; 0 only U labels' counts; 1 only V labels'
+  uint64_t *wedges = nullptr;    // device counter of traversed wedges (optional)
+};
+// Alg. 1 over the labelled adjacency (all starts).
+void count_butterflies(Arena &a, const Graph &G, const CountOut &o);
+
+// side flags of labels: isU[label] = 1 if the label is a U vertex
+uint8_t *label_sides(Arena &a, const Graph &G);
+
+// ------------------------------------------------------------------ tip
+struct TipParams {
+  uint32_t P;
+  int bounds_mode;
+  const uint64_t *bounds;
+  uint32_t n_bounds;
+  int recount, compact, graph_rounds;
+  uint64_t timeout_ns;
+};
+void tip_decompose(Arena &a, Graph &G, int side, const TipParams &p, uint64_t *theta_out, pbng_stats *st);
+
+// ------------------------------------------------------------------ wing
+void wing_decompose(Arena &a, Graph &G, const TipParams &p, uint64_t *theta_out, pbng_stats *st);
+
+}  // namespace pbng

@@ -1,0 +1,1057 @@
+// Tip decomposition with two-phase peeling (Sec. 3.1, adapted to tips in
+// Sec. 3.2).  X = the peeled vertex side, Y = the other side (never peeled).
+//
+// Coarse phase (Sec. 3.1.1, Alg. 4 with the tip adaptation of Sec. 3.2):
+//  for each range i: theta(i+1) from find_range (Sec. 3.1.3) or an explicit
+//  bound; snapshot supports into init (the support initialisation vector);
+//  then peel rounds: the active set is every unpeeled vertex with support
+//  below theta(i+1).  A round either
+//   - peels the active set: every wedge x -> y -> x' from an active x to an
+//     unpeeled x' is counted per pair, and support(x') -= C(c(x,x'), 2)
+//     (updates from different active vertices are disjoint butterflies and
+//     are summed atomically, Sec. 3.2), or
+//   - re-counts the butterflies of all remaining vertices when the active
+//     set's wedges exceed the counting bound (batch processing, Sec. 5.1).
+//  Edges to peeled vertices are removed from the Y-side lists after each
+//  round (dynamic graph updates, Sec. 5.2).  Supports are kept exact
+//  (unclamped); the clamp of Alg. 2 only matters when a number is recorded.
+// Fine phase (Sec. 3.1.2, 3.1.4, 3.2): partition i is peeled bottom-up from
+//  init on the subgraph induced on (X_i, Y): one thread block per partition,
+//  partitions handed out heaviest first (LPT) from a device queue; each step
+//  peels every vertex whose support equals the running minimum (ties receive
+//  the same number, exactly as one-at-a-time peeling with the clamp).
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+#include "wedge.cuh"
+
+namespace pbng {
+namespace {
+
+enum : uint8_t { ST_ALIVE = 0, ST_ACTIVE = 1, ST_PEELED = 2 };
+
+constexpr uint32_t PW_MAXW = 256, PW_CAP = 512;    // warp-per-vertex, shared hash
+constexpr uint32_t PB_MAXW = 4096, PB_CAP = 8192;  // block-per-vertex, shared hash
+constexpr uint32_t P_DENSE = 16384;                // dense shared counters when ids < this
+constexpr int PBT = 512, PWT = 256;
+enum { PC_WARP = 0, PC_BDENSE = 1, PC_BHASH = 2, PC_GLOBAL = 3, PNCLASS = 4 };
+
+using ull = unsigned long long;
+
+// ------------------------------------------------------------ peel kernels
+struct PeelArgs {
+  const uint32_t *p_off, *p_adj;  // X -> Y
+  const uint32_t *o_off, *o_adj, *o_len;  // Y -> X (current)
+  uint8_t *state;
+  ull *sup;
+  const ull *theta_hi;
+  uint32_t *next;
+  unsigned *next_n;
+  ull *updates;
+  uint32_t nx;
+};
+
+template <int N>
+struct PMid {
+  uint32_t lo[N];
+  uint32_t pre[N + 1];
+};
+
+template <class Grp, int N>
+__device__ __forceinline__ uint32_t peel_load(const PeelArgs &A, uint32_t xo, uint32_t xd, uint32_t base, const Grp &g,
+                                              PMid<N> &mb) {
+  int r = g.rank();
+  uint32_t lo = 0, len = 0;
+  if (base + r < xd) {
+    uint32_t y = A.p_adj[xo + base + r];
+    lo = A.o_off[y];
+    len = A.o_len[y];
+  }
+  mb.lo[r] = lo;
+  return g.scan(len, mb.pre);
+}
+
+template <class Grp, int N, class F>
+__device__ __forceinline__ void peel_walk(const PeelArgs &A, const Grp &g, const PMid<N> &mb, uint32_t T, F &&f) {
+  for (uint32_t w = g.rank(); w < T; w += N) {
+    int i = seg_of(mb.pre, N, w);
+    f(A.o_adj[mb.lo[i] + (w - mb.pre[i])]);
+  }
+}
+
+__device__ __forceinline__ void dec_support(const PeelArgs &A, uint32_t xp, uint64_t dec, uint64_t thi) {
+  ull old = atomicAdd(&A.sup[xp], (ull)(0ull - dec));
+  if (old >= thi && old - dec < thi) {
+    unsigned p = atomicAdd(A.next_n, 1u);
+    A.next[p] = xp;
+  }
+}
+
+struct PHash {
+  SmemHash h;
+  uint32_t cap;
+  __device__ void inc(uint32_t k) const { h.inc(k); }
+  template <class Grp, int N>
+  __device__ uint64_t drain(const PeelArgs &A, uint32_t, uint32_t, const Grp &g, PMid<N> &, uint64_t thi) const {
+    uint64_t nup = 0;
+    for (uint32_t i = g.rank(); i < cap; i += N) {
+      uint32_t k = h.key[i];
+      if (k != EMPTY_KEY) {
+        uint32_t c = h.val[i];
+        if (c >= 2) {
+          dec_support(A, k, choose2(c), thi);
+          nup++;
+        }
+        h.key[i] = EMPTY_KEY;
+        h.val[i] = 0;
+      }
+    }
+    return nup;
+  }
+};
+
+struct PDense {  // dense counters indexed by vertex id (shared or global memory)
+  uint32_t *c;
+  __device__ void inc(uint32_t k) const { atomicAdd(&c[k], 1u); }
+  template <class Grp, int N>
+  __device__ uint64_t drain(const PeelArgs &A, uint32_t xo, uint32_t xd, const Grp &g, PMid<N> &mb, uint64_t thi) const {
+    uint64_t nup = 0;
+    for (uint32_t base = 0; base < xd; base += N) {
+      uint32_t T = peel_load(A, xo, xd, base, g, mb);
+      peel_walk(A, g, mb, T, [&](uint32_t xp) {
+        if (A.state[xp] != ST_ALIVE) return;
+        uint32_t x = atomicExch(&c[xp], 0u);
+        if (x >= 2) {
+          dec_support(A, xp, choose2(x), thi);
+          nup++;
+        }
+      });
+      g.sync();
+    }
+    return nup;
+  }
+};
+
+template <class Grp, int N, class Tbl>
+__device__ void peel_vertex(const PeelArgs &A, uint32_t x, const Grp &g, PMid<N> &mb, const Tbl &tbl, uint64_t thi) {
+  uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
+  for (uint32_t base = 0; base < xd; base += N) {
+    uint32_t T = peel_load(A, xo, xd, base, g, mb);
+    peel_walk(A, g, mb, T, [&](uint32_t xp) {
+      if (A.state[xp] == ST_ALIVE) tbl.inc(xp);
+    });
+    g.sync();
+  }
+  uint64_t nup = tbl.drain(A, xo, xd, g, mb, thi);
+  g.sync();
+  uint64_t t = g.sum64(nup);
+  if (g.rank() == 0 && t && A.updates) atomicAdd(A.updates, (ull)t);
+}
+
+__global__ void __launch_bounds__(PWT) k_peel_warp(PeelArgs A, const uint64_t *list, const unsigned *count) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr size_t per = align16(PW_CAP * 8 + sizeof(PMid<32>));
+  uint32_t *key = (uint32_t *)(sm + w * per), *val = key + PW_CAP;
+  PMid<32> &mb = *(PMid<32> *)(sm + w * per + PW_CAP * 8);
+  for (uint32_t i = lane; i < PW_CAP; i += 32) key[i] = EMPTY_KEY, val[i] = 0;
+  __syncwarp();
+  WarpGrp g;
+  uint64_t thi = *A.theta_hi;
+  unsigned n = *count;
+  for (size_t it = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; it < n; it += ((size_t)gridDim.x * blockDim.x) >> 5) {
+    uint64_t item = list[it];
+    uint32_t x = (uint32_t)item, W = (uint32_t)(item >> 32);
+    uint32_t cap = pow2_at_least(max(2u * W, 32u));
+    PHash p{SmemHash{key, val, cap - 1}, cap};
+    peel_vertex(A, x, g, mb, p, thi);
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(PBT) k_peel_block(PeelArgs A, const uint64_t *list, const unsigned *count,
+                                                     uint32_t *gscratch) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  PMid<PBT> &mb = *(PMid<PBT> *)sm;
+  constexpr size_t o1 = align16(sizeof(PMid<PBT>));
+  uint32_t *ws = (uint32_t *)(sm + o1);
+  ull *ws64 = (ull *)(sm + o1 + 128);
+  uint8_t *tb = sm + o1 + 256;
+  BlockGrp<PBT> g{ws, ws64};
+  if (KIND == PC_BDENSE) {
+    uint32_t *c = (uint32_t *)tb;
+    for (uint32_t i = threadIdx.x; i < P_DENSE; i += PBT) c[i] = 0;
+  } else if (KIND == PC_BHASH) {
+    uint32_t *key = (uint32_t *)tb;
+    for (uint32_t i = threadIdx.x; i < PB_CAP; i += PBT) key[i] = EMPTY_KEY, key[PB_CAP + i] = 0;
+  }
+  __syncthreads();
+  uint64_t thi = *A.theta_hi;
+  unsigned n = *count;
+  for (size_t it = blockIdx.x; it < n; it += gridDim.x) {
+    uint64_t item = list[it];
+    uint32_t x = (uint32_t)item, W = (uint32_t)(item >> 32);
+    if (KIND == PC_BDENSE) {
+      PDense p{(uint32_t *)tb};
+      peel_vertex(A, x, g, mb, p, thi);
+    } else if (KIND == PC_BHASH) {
+      uint32_t cap = pow2_at_least(max(2u * W, 64u));
+      uint32_t *key = (uint32_t *)tb;
+      PHash p{SmemHash{key, key + PB_CAP, cap - 1}, cap};
+      peel_vertex(A, x, g, mb, p, thi);
+    } else {
+      PDense p{gscratch + (size_t)blockIdx.x * A.nx};
+      peel_vertex(A, x, g, mb, p, thi);
+    }
+  }
+}
+
+size_t peel_block_smem(int kind) {
+  size_t s = align16(sizeof(PMid<PBT>)) + 256;
+  if (kind == PC_BDENSE) s += P_DENSE * 4;
+  if (kind == PC_BHASH) s += PB_CAP * 8;
+  return s;
+}
+
+// ------------------------------------------------------- round bookkeeping
+struct PrepArgs {
+  const uint32_t *frontier;
+  uint32_t nf;
+  const uint32_t *p_off, *p_adj, *o_len;
+  uint32_t *part;
+  uint32_t pi;
+  uint32_t *ytouch, *touched;
+  unsigned *touched_n;
+  int compact;
+  ull *sum_w;
+  uint64_t *lists;  // PNCLASS x nx
+  unsigned *counts;
+  uint32_t nx;
+  int small_ids;    // nx <= P_DENSE
+};
+
+// one warp per active vertex: partition id, wedge count, class, touched Y lists
+__global__ void k_prep(PrepArgs A) {
+  int lane = threadIdx.x & 31;
+  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t j = gw; j < A.nf; j += nw) {
+    uint32_t x = A.frontier[j];
+    uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
+    uint64_t W = 0;
+    for (uint32_t k = lane; k < xd; k += 32) {
+      uint32_t y = A.p_adj[xo + k];
+      W += A.o_len[y];
+      if (A.compact && atomicExch(&A.ytouch[y], 1u) == 0u) {
+        unsigned p = atomicAdd(A.touched_n, 1u);
+        A.touched[p] = y;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
+    if (lane == 0) {
+      A.part[x] = A.pi;
+      atomicAdd(A.sum_w, (ull)W);
+      if (W >= 2) {
+        int c = W <= PW_MAXW ? PC_WARP : (A.small_ids ? PC_BDENSE : (W <= PB_MAXW ? PC_BHASH : PC_GLOBAL));
+        unsigned p = atomicAdd(&A.counts[c], 1u);
+        A.lists[(size_t)c * A.nx + p] = (uint64_t)x | ((uint64_t)min(W, (uint64_t)0xffffffffu) << 32);
+      }
+    }
+  }
+}
+
+__global__ void k_mark_peeled(const uint32_t *f, uint32_t nf, uint8_t *state, uint8_t *lab_alive, const uint32_t *x2lab) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < nf; j += (size_t)gridDim.x * blockDim.x) {
+    uint32_t x = f[j];
+    state[x] = ST_PEELED;
+    if (lab_alive) lab_alive[x2lab[x]] = 0;
+  }
+}
+
+// warp per touched Y vertex: stable in-place removal of peeled X entries
+__global__ void k_compact(const uint32_t *touched, const unsigned *tn, const uint32_t *o_off, uint32_t *o_adj, uint32_t *o_len,
+                          uint32_t *ytouch, const uint8_t *state) {
+  int lane = threadIdx.x & 31;
+  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  unsigned n = *tn;
+  for (size_t j = gw; j < n; j += nw) {
+    uint32_t y = touched[j];
+    uint32_t lo = o_off[y], len = o_len[y], out = 0;
+    for (uint32_t k = 0; k < len; k += 32) {
+      uint32_t x = 0;
+      bool keep = false;
+      if (k + lane < len) {
+        x = o_adj[lo + k + lane];
+        keep = state[x] == ST_ALIVE;
+      }
+      unsigned b = __ballot_sync(0xffffffffu, keep);
+      __syncwarp();
+      if (keep) o_adj[lo + out + __popc(b & ((1u << lane) - 1u))] = x;
+      out += __popc(b);
+      __syncwarp();
+    }
+    if (lane == 0) {
+      o_len[y] = out;
+      ytouch[y] = 0;
+    }
+  }
+}
+
+// -------------------------------------------------- partition bookkeeping
+// keep alive entries of the remaining list
+__global__ void k_compact_list(const uint32_t *in, uint32_t n, const uint8_t *state, uint32_t *out, unsigned *on) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x) {
+    uint32_t x = in[j];
+    bool keep = state[x] == ST_ALIVE;
+    unsigned b = __ballot_sync(__activemask(), keep);
+    int lane = threadIdx.x & 31, leader = __ffs(__activemask()) - 1;
+    unsigned base = 0;
+    if (lane == leader && b) base = atomicAdd(on, __popc(b));
+    base = __shfl_sync(__activemask(), base, leader);
+    if (keep) out[base + __popc(b & ((1u << lane) - 1u))] = x;
+  }
+}
+
+struct RangeState {  // device-side state of find_range
+  ull kmin, kmax, wsum;  // filled by k_weights
+  ull prefix, below, tgt, est, theta_hi;
+  ull hist[256];
+};
+
+// warp per remaining vertex: work proxy w = wedges of x on the current graph
+// (Sec. 3.2), key range and total work
+__global__ void k_weights(const uint32_t *alist, uint32_t na, const uint32_t *p_off, const uint32_t *p_adj,
+                          const uint32_t *o_len, const ull *sup, ull *wl, RangeState *rs) {
+  int lane = threadIdx.x & 31;
+  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  ull mn = ~0ull, mx = 0, ws = 0;
+  for (size_t j = gw; j < na; j += nw) {
+    uint32_t x = alist[j];
+    uint32_t xo = p_off[x], xd = p_off[x + 1] - xo;
+    ull W = 0;
+    for (uint32_t k = lane; k < xd; k += 32) W += o_len[p_adj[xo + k]];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
+    if (lane == 0) {
+      wl[j] = W;
+      ull s = sup[x];
+      mn = min(mn, s);
+      mx = max(mx, s);
+      ws += W;
+    }
+  }
+  if (lane == 0) {
+    atomicMin(&rs->kmin, mn);
+    atomicMax(&rs->kmax, mx);
+    if (ws) atomicAdd(&rs->wsum, ws);
+  }
+}
+
+// histogram of work by the digit at `shift` among keys matching the prefix
+__global__ void k_range_hist(const uint32_t *alist, uint32_t na, const ull *sup, const ull *wl, RangeState *rs, int shift) {
+  __shared__ ull h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  ull prefix = rs->prefix;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < na; j += (size_t)gridDim.x * blockDim.x) {
+    ull key = sup[alist[j]];
+    if (shift + 8 >= 64 || ((key ^ prefix) >> (shift + 8)) == 0) {
+      ull w = wl[j];
+      if (w) atomicAdd(&h[(key >> shift) & 255u], w);
+    }
+  }
+  __syncthreads();
+  if (h[threadIdx.x]) atomicAdd(&rs->hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// choose the digit where the cumulative work first reaches the target
+__global__ void k_range_select(RangeState *rs, int shift, int last) {
+  if (threadIdx.x != 0) return;
+  ull cum = rs->below;
+  int d = 255;
+  for (int i = 0; i < 256; i++) {
+    if (cum + rs->hist[i] >= rs->tgt) {
+      d = i;
+      break;
+    }
+    cum += rs->hist[i];
+  }
+  ull est = cum + rs->hist[d];
+  rs->below = cum;
+  rs->prefix = (rs->prefix & ~(255ull << shift)) | ((ull)d << shift);
+  for (int i = 0; i < 256; i++) rs->hist[i] = 0;
+  if (last) {
+    rs->est = est;
+    rs->theta_hi = rs->prefix + 1;
+  }
+}
+
+__global__ void k_set_u64(ull *p, ull v) { *p = v; }
+
+// start of a range (snapshot = 1): init <- support; any pass: the active set
+// is every unpeeled vertex with support below theta_hi
+__global__ void k_scan_frontier(const uint32_t *alist, uint32_t na, uint8_t *state, const ull *sup, ull *init,
+                                const ull *theta_hi, int snapshot, uint32_t *f, unsigned *fn) {
+  ull thi = *theta_hi;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < na; j += (size_t)gridDim.x * blockDim.x) {
+    uint32_t x = alist[j];
+    if (state[x] != ST_ALIVE) continue;
+    ull s = sup[x];
+    if (snapshot) init[x] = s;
+    if (s < thi) {
+      state[x] = ST_ACTIVE;
+      unsigned p = atomicAdd(fn, 1u);
+      f[p] = x;
+    }
+  }
+}
+
+__global__ void k_gather_counts(const uint32_t *alist, uint32_t na, const uint8_t *state, const uint32_t *x2lab,
+                                const ull *cnt_lab, ull *sup) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < na; j += (size_t)gridDim.x * blockDim.x) {
+    uint32_t x = alist[j];
+    if (state[x] == ST_ALIVE) sup[x] = cnt_lab[x2lab[x]];
+  }
+}
+
+__global__ void k_degrees(const uint32_t *off, uint32_t n, uint32_t *len) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    len[i] = off[i + 1] - off[i];
+}
+
+__global__ void k_init_side(uint32_t nx, const uint32_t *x2lab, const ull *cnt_lab, ull *sup, uint32_t *alist) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < nx; x += (size_t)gridDim.x * blockDim.x) {
+    sup[x] = cnt_lab[x2lab[x]];
+    alist[x] = (uint32_t)x;
+  }
+}
+
+__global__ void k_x2lab(const uint32_t *g2lab, uint32_t off, uint32_t nx, uint32_t *x2lab) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < nx; x += (size_t)gridDim.x * blockDim.x)
+    x2lab[x] = g2lab[off + x];
+}
+
+// ------------------------------------------------------------ fine phase
+struct FDArgs {
+  const uint32_t *p_off, *p_adj;  // X -> Y
+  const uint32_t *o_off;          // Y segments in the partitioned adjacency
+  const uint32_t *fd_adj, *fd_part;  // Y -> X grouped by (y, part(x)), x ascending
+  const uint32_t *xs, *ps, *loc;  // X ids grouped by partition; partition offsets; local index
+  const uint32_t *order;          // partitions, heaviest first
+  uint32_t nparts;
+  uint8_t *state;
+  ull *sup;  // starts as init
+  ull *theta;
+  uint32_t *buf_a, *buf_b, *buf_f, *buf_big;  // per-partition regions (offset ps[p])
+  uint32_t *gcnt;                             // per-partition dense counters (offset ps[p]), zeroed
+  unsigned *queue;
+  ull *wedges, *steps, *updates;
+};
+
+constexpr int FT = 512, FW = FT / 32;
+
+template <int N>
+struct FMid {
+  uint32_t lo[N];
+  uint32_t pre[N + 1];
+};
+
+// segment of y's partitioned list holding partition p
+__device__ __forceinline__ void fd_seg(const FDArgs &A, uint32_t y, uint32_t p, uint32_t &lo, uint32_t &len) {
+  uint32_t b = A.o_off[y], e = A.o_off[y + 1];
+  uint32_t l0 = b + lower_bound_u32(A.fd_part + b, e - b, p);
+  uint32_t l1 = l0 + lower_bound_u32(A.fd_part + l0, e - l0, p + 1);
+  lo = l0;
+  len = l1 - l0;
+}
+
+template <class Grp, int N>
+__device__ __forceinline__ uint32_t fd_load(const FDArgs &A, uint32_t p, uint32_t xo, uint32_t xd, uint32_t base,
+                                            const Grp &g, FMid<N> &mb) {
+  int r = g.rank();
+  uint32_t lo = 0, len = 0;
+  if (base + r < xd) fd_seg(A, A.p_adj[xo + base + r], p, lo, len);
+  mb.lo[r] = lo;
+  return g.scan(len, mb.pre);
+}
+
+template <class Grp, int N, class F>
+__device__ __forceinline__ void fd_walk(const FDArgs &A, const Grp &g, const FMid<N> &mb, uint32_t T, F &&f) {
+  for (uint32_t w = g.rank(); w < T; w += N) {
+    int i = seg_of(mb.pre, N, w);
+    f(A.fd_adj[mb.lo[i] + (w - mb.pre[i])]);
+  }
+}
+
+__device__ __forceinline__ uint8_t ld_state(const uint8_t *s) { return *(volatile const uint8_t *)s; }
+
+__global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size_t dense_off) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ uint32_t s_p, s_na, s_nf, s_nr, s_fidx, s_nbig;
+  __shared__ ull s_min, s_level;
+  __shared__ uint32_t ws[FT / 32 + 2];
+  __shared__ ull ws64[FT / 32];
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t *wkey = (uint32_t *)(sm + warp * warp_bytes), *wval = wkey + PW_CAP;
+  FMid<32> &wmb = *(FMid<32> *)(sm + warp * warp_bytes + PW_CAP * 8);
+  FMid<FT> &bmb = *(FMid<FT> *)(sm + FW * warp_bytes);
+  uint32_t *dense = (uint32_t *)(sm + dense_off);
+  for (uint32_t i = lane; i < PW_CAP; i += 32) wkey[i] = EMPTY_KEY, wval[i] = 0;
+  for (uint32_t i = threadIdx.x; i < P_DENSE; i += FT) dense[i] = 0;
+  __syncthreads();
+  WarpGrp wg;
+  BlockGrp<FT> bg{ws, ws64};
+  ull my_wedges = 0, my_updates = 0, my_steps = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      unsigned q = atomicAdd(A.queue, 1u);
+      s_p = q < A.nparts ? A.order[q] : 0xffffffffu;
+    }
+    __syncthreads();
+    uint32_t p = s_p;
+    if (p == 0xffffffffu) break;
+    uint32_t base = A.ps[p], np = A.ps[p + 1] - base;
+    uint32_t *la = A.buf_a + base, *lb = A.buf_b + base, *lf = A.buf_f + base, *lbig = A.buf_big + base;
+    bool smem_dense = np <= P_DENSE;
+    uint32_t *cnt = smem_dense ? dense : A.gcnt + base;
+    for (uint32_t j = threadIdx.x; j < np; j += FT) la[j] = A.xs[base + j];
+    if (threadIdx.x == 0) {
+      s_na = np;
+      s_level = 0;
+    }
+    __syncthreads();
+    while (s_na > 0) {
+      uint32_t na = s_na;
+      // running minimum of the remaining supports
+      if (threadIdx.x == 0) s_min = ~0ull;
+      __syncthreads();
+      ull mn = ~0ull;
+      for (uint32_t j = threadIdx.x; j < na; j += FT) mn = min(mn, __ldcg(&A.sup[la[j]]));
+#pragma unroll
+      for (int o = 16; o; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      if (lane == 0) atomicMin(&s_min, mn);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_level = max(s_level, s_min);
+        s_nf = 0;
+        s_nr = 0;
+        s_fidx = 0;
+        s_nbig = 0;
+      }
+      __syncthreads();
+      ull level = s_level;
+      // every vertex at the minimum is peeled with tip number = level
+      for (uint32_t j = threadIdx.x; j < na; j += FT) {
+        uint32_t x = la[j];
+        ull s = __ldcg(&A.sup[x]);
+        if (s <= level) {
+          lf[atomicAdd(&s_nf, 1u)] = x;
+          A.theta[x] = level;
+          A.state[x] = ST_PEELED;
+        } else {
+          lb[atomicAdd(&s_nr, 1u)] = x;
+        }
+      }
+      __syncthreads();
+      uint32_t nf = s_nf;
+      my_steps++;
+      // warp-per-vertex updates for vertices with few wedges in G_p
+      for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(&s_fidx, 1u);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= nf) break;
+        uint32_t x = lf[k];
+        uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
+        uint32_t W = 0;
+        for (uint32_t b0 = 0; b0 < xd; b0 += 32) {
+          uint32_t lo = 0, len = 0;
+          if (b0 + lane < xd) fd_seg(A, A.p_adj[xo + b0 + lane], p, lo, len);
+#pragma unroll
+          for (int o = 16; o; o >>= 1) len += __shfl_xor_sync(0xffffffffu, len, o);
+          W += len;
+        }
+        if (W < 2) continue;
+        if (W > PW_MAXW) {
+          if (lane == 0) lbig[atomicAdd(&s_nbig, 1u)] = x;
+          continue;
+        }
+        my_wedges += lane == 0 ? W : 0;
+        uint32_t cap = pow2_at_least(max(2u * W, 32u));
+        SmemHash h{wkey, wval, cap - 1};
+        for (uint32_t b0 = 0; b0 < xd; b0 += 32) {
+          uint32_t T = fd_load(A, p, xo, xd, b0, wg, wmb);
+          fd_walk(A, wg, wmb, T, [&](uint32_t xp) {
+            if (ld_state(&A.state[xp]) == ST_ALIVE) h.inc(xp);
+          });
+          __syncwarp();
+        }
+        for (uint32_t i = lane; i < cap; i += 32) {
+          uint32_t kk = wkey[i];
+          if (kk != EMPTY_KEY) {
+            uint32_t c = wval[i];
+            if (c >= 2) {
+              atomicAdd(&A.sup[kk], (ull)(0ull - choose2(c)));
+              my_updates++;
+            }
+            wkey[i] = EMPTY_KEY;
+            wval[i] = 0;
+          }
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      // block-per-vertex updates with dense counters over the partition
+      uint32_t nbig = s_nbig;
+      for (uint32_t bi = 0; bi < nbig; bi++) {
+        uint32_t x = lbig[bi];
+        uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
+        for (uint32_t b0 = 0; b0 < xd; b0 += FT) {
+          uint32_t T = fd_load(A, p, xo, xd, b0, bg, bmb);
+          if (threadIdx.x == 0) my_wedges += T;
+          fd_walk(A, bg, bmb, T, [&](uint32_t xp) {
+            if (ld_state(&A.state[xp]) == ST_ALIVE) atomicAdd(&cnt[A.loc[xp]], 1u);
+          });
+          __syncthreads();
+        }
+        for (uint32_t b0 = 0; b0 < xd; b0 += FT) {
+          uint32_t T = fd_load(A, p, xo, xd, b0, bg, bmb);
+          fd_walk(A, bg, bmb, T, [&](uint32_t xp) {
+            if (ld_state(&A.state[xp]) != ST_ALIVE) return;
+            uint32_t c = atomicExch(&cnt[A.loc[xp]], 0u);
+            if (c >= 2) {
+              atomicAdd(&A.sup[xp], (ull)(0ull - choose2(c)));
+              my_updates++;
+            }
+          });
+          __syncthreads();
+        }
+      }
+      if (threadIdx.x == 0) s_na = s_nr;
+      uint32_t *t = la;
+      la = lb;
+      lb = t;
+      __syncthreads();
+    }
+  }
+  my_wedges = bg.sum64(my_wedges);
+  my_updates = bg.sum64(my_updates);
+  if (threadIdx.x == 0) {
+    if (A.wedges) atomicAdd(A.wedges, my_wedges);
+    if (A.updates) atomicAdd(A.updates, my_updates);
+    if (A.steps) atomicAdd(A.steps, my_steps);
+  }
+}
+
+size_t fd_warp_bytes() { return align16(PW_CAP * 8 + sizeof(FMid<32>)); }
+size_t fd_dense_off() { return align16(FW * fd_warp_bytes() + sizeof(FMid<FT>)); }
+size_t fd_smem() { return fd_dense_off() + P_DENSE * 4; }
+
+// FD adjacency keys: (y, part(x)) for every Y-side entry
+__global__ void k_fd_keys(const uint32_t *o_off, const uint32_t *o_adj0, uint32_t ny, const uint32_t *part, int bp,
+                          uint64_t *key, uint32_t *val) {
+  int lane = threadIdx.x & 31;
+  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t y = gw; y < ny; y += nw)
+    for (uint32_t k = o_off[y] + lane; k < o_off[y + 1]; k += 32) {
+      uint32_t x = o_adj0[k];
+      key[k] = ((uint64_t)y << bp) | part[x];
+      val[k] = x;
+    }
+}
+
+__global__ void k_fd_part_of(const uint32_t *fd_adj, uint32_t m, const uint32_t *part, uint32_t *fd_part) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x)
+    fd_part[k] = part[fd_adj[k]];
+}
+
+// work of partition p: wedges of G_p with both endpoints in X_p (Sec. 3.2),
+// sum over groups (y, p) of size*(size-1)
+__global__ void k_fd_work(const uint32_t *o_off, uint32_t ny, const uint32_t *fd_part, ull *work) {
+  int lane = threadIdx.x & 31;
+  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t y = gw; y < ny; y += nw) {
+    uint32_t b = o_off[y], e = o_off[y + 1];
+    for (uint32_t k = b + lane; k < e; k += 32) {
+      if (k == b || fd_part[k] != fd_part[k - 1]) {  // group head
+        uint32_t p = fd_part[k];
+        uint32_t len = lower_bound_u32(fd_part + k, e - k, p + 1);
+        if (len >= 2) atomicAdd(&work[p], (ull)len * (len - 1));
+      }
+    }
+  }
+}
+
+__global__ void k_part_hist(const uint32_t *part, uint32_t nx, uint32_t *cnt) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < nx; x += (size_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[part[x]], 1u);
+}
+
+__global__ void k_part_keys(const uint32_t *part, uint32_t nx, uint64_t *key, uint32_t *val) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < nx; x += (size_t)gridDim.x * blockDim.x) {
+    key[x] = part[x];
+    val[x] = (uint32_t)x;
+  }
+}
+
+__global__ void k_loc(const uint32_t *xs, uint32_t nx, const uint32_t *part, const uint32_t *ps, uint32_t *loc, uint8_t *state) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < nx; j += (size_t)gridDim.x * blockDim.x) {
+    uint32_t x = xs[j];
+    loc[x] = (uint32_t)(j - ps[part[x]]);
+    state[x] = ST_ALIVE;
+  }
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- driver
+void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t *theta_out, pbng_stats *st) {
+  const int T = 256;
+  const int sms = num_sms();
+  const unsigned cap = 16 * sms;
+  uint32_t nx = side == 0 ? G.nu : G.nv, ny = side == 0 ? G.nv : G.nu;
+  if (nx == 0) return;
+  if (G.m == 0) {
+    CK(cudaMemsetAsync(theta_out, 0, (size_t)nx * 8, a.st));
+    return;
+  }
+  const uint32_t *p_off = side == 0 ? G.u_off : G.v_off, *p_adj = side == 0 ? G.u_adj : G.v_adj;
+  const uint32_t *o_off = side == 0 ? G.v_off : G.u_off, *o_adj0 = side == 0 ? G.v_adj : G.u_adj;
+  cudaEvent_t ev[6];
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(ev[0], a.st));
+
+  // ---- initial supports by Alg. 1 (counts of the peeled side only)
+  ull *dwedge = a.zeros<ull>(8);  // [0] count, [1] recount, [2] fd wedges, [3] fd steps, [4] updates
+  uint8_t *isU = label_sides(a, G);
+  ull *cnt_lab = a.zeros<ull>(G.n);
+  CountOut co;
+  co.cnt_lab = (uint64_t *)cnt_lab;
+  co.lab_isU = isU;
+  co.want_side = side;
+  co.wedges = (uint64_t *)dwedge;
+  count_butterflies(a, G, co);
+  uint32_t *x2lab = a.alloc<uint32_t>(nx);
+  k_x2lab<<<grid_for(nx, T, cap), T, 0, a.st>>>(G.g2lab, side == 0 ? 0 : G.nu, nx, x2lab);
+  CK_LAUNCH();
+  ull *sup = a.alloc<ull>(nx), *init = a.alloc<ull>(nx);
+  uint32_t *alist = a.alloc<uint32_t>(nx), *alist2 = a.alloc<uint32_t>(nx);
+  k_init_side<<<grid_for(nx, T, cap), T, 0, a.st>>>(nx, x2lab, cnt_lab, sup, alist);
+  CK_LAUNCH();
+  CK(cudaEventRecord(ev[1], a.st));
+
+  // ---- coarse phase state
+  uint8_t *state = a.zeros<uint8_t>(nx);
+  uint8_t *lab_alive = nullptr;
+  if (prm.recount) {
+    lab_alive = a.alloc<uint8_t>(G.n);
+    CK(cudaMemsetAsync(lab_alive, 1, G.n, a.st));
+  }
+  uint32_t *part = a.alloc<uint32_t>(nx);
+  uint32_t *o_adj = a.alloc<uint32_t>(G.m), *o_len = a.alloc<uint32_t>(ny + 1);
+  CK(cudaMemcpyAsync(o_adj, o_adj0, (size_t)G.m * 4, cudaMemcpyDeviceToDevice, a.st));
+  k_degrees<<<grid_for(ny, T, cap), T, 0, a.st>>>(o_off, ny, o_len);
+  CK_LAUNCH();
+  uint32_t *ytouch = a.zeros<uint32_t>(ny + 1), *touched = a.alloc<uint32_t>(ny + 1);
+  uint32_t *front = a.alloc<uint32_t>(nx), *front2 = a.alloc<uint32_t>(nx);
+  uint64_t *plists = a.alloc<uint64_t>((size_t)PNCLASS * nx);
+  // small device counters: [0] frontier size, [1] next size, [2] touched, [3..6] class counts, [7] alist size
+  unsigned *dc = a.zeros<unsigned>(16);
+  ull *sumw = a.zeros<ull>(2);
+  RangeState *rs = a.zeros<RangeState>(1);
+  ull *wl = a.alloc<ull>(nx);
+  uint32_t *gscr = nullptr;  // per-block dense counters for the heaviest vertices
+  unsigned gscr_blocks = 2 * sms;
+  bool small_ids = nx <= P_DENSE;
+
+  PeelArgs PA;
+  PA.p_off = p_off;
+  PA.p_adj = p_adj;
+  PA.o_off = o_off;
+  PA.o_adj = o_adj;
+  PA.o_len = o_len;
+  PA.state = state;
+  PA.sup = sup;
+  PA.theta_hi = &rs->theta_hi;
+  PA.updates = dwedge + 4;
+  PA.nx = nx;
+
+  static bool attr = false;
+  size_t wsm = (PWT / 32) * align16(PW_CAP * 8 + sizeof(PMid<32>));
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_peel_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+    CK(cudaFuncSetAttribute(k_peel_block<PC_BDENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)peel_block_smem(PC_BDENSE)));
+    CK(cudaFuncSetAttribute(k_peel_block<PC_BHASH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)peel_block_smem(PC_BHASH)));
+    CK(cudaFuncSetAttribute(k_peel_block<PC_GLOBAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)peel_block_smem(PC_GLOBAL)));
+    CK(cudaFuncSetAttribute(k_fd_tip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fd_smem()));
+    attr = true;
+  }
+
+  uint32_t na = nx;
+  uint32_t pi = 0;
+  double scale = 1.0;
+  uint64_t prev_init_est = 0, cur_final = 0;
+  uint64_t rounds = 0, recounts = 0, wedges_cd = 0;
+  uint64_t wbound = G.wedge_bound;
+  uint32_t P = prm.P;
+  while (na > 0) {
+    // ---- remaining list (drop peeled vertices)
+    if (pi > 0) {
+      CK(cudaMemsetAsync(dc + 7, 0, 4, a.st));
+      k_compact_list<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, alist2, dc + 7);
+      CK_LAUNCH();
+      na = fetch(a, dc + 7);
+      std::swap(alist, alist2);
+      if (na == 0) break;
+    }
+    // ---- range [theta(i), theta(i+1)) (Alg. 4 l.8, Sec. 3.1.3)
+    bool last = pi + 1 >= P;
+    CK(cudaMemsetAsync(rs, 0, sizeof(RangeState), a.st));
+    k_set_u64<<<1, 1, 0, a.st>>>(&rs->kmin, ~0ull);
+    k_weights<<<grid_for((size_t)na * 32, T, cap), T, 0, a.st>>>(alist, na, p_off, p_adj, o_len, sup, wl, rs);
+    CK_LAUNCH();
+    ull hk[3];
+    CK(cudaMemcpyAsync(hk, &rs->kmin, sizeof(hk), cudaMemcpyDeviceToHost, a.st));
+    CK(cudaStreamSynchronize(a.st));
+    ull kmin = hk[0], kmax = hk[1], wsum = hk[2];
+    // adaptive target (Sec. 3.1.3): remaining work over remaining partitions,
+    // scaled by how far the previous partition overshot its estimate
+    if (pi > 0 && cur_final > 0) {
+      scale = (double)prev_init_est / (double)cur_final;
+      if (scale > 1.0) scale = 1.0;
+      if (scale <= 0.0) scale = 1.0;
+    }
+    ull thi;
+    bool use_est = true;
+    if (last) {
+      thi = ~0ull;
+      use_est = false;
+    } else if (prm.bounds_mode == PBNG_BOUNDS_EXPLICIT && pi < prm.n_bounds && prm.bounds[pi] > kmin) {
+      thi = prm.bounds[pi];
+      use_est = false;
+    }
+    uint64_t init_est = 0;
+    if (use_est) {
+      if (wsum == 0 || kmin == kmax) {
+        thi = kmin + 1;
+        init_est = wsum;
+        k_set_u64<<<1, 1, 0, a.st>>>(&rs->theta_hi, thi);
+      } else {
+        double t = (double)wsum * scale / (double)(P - pi);
+        ull tgt = t < 1.0 ? 1 : (t >= (double)wsum ? wsum : (ull)t);
+        k_set_u64<<<1, 1, 0, a.st>>>(&rs->tgt, tgt);
+        int hb = 64 - __builtin_clzll(kmin ^ kmax);  // low bits in which keys differ
+        ull low = hb >= 64 ? ~0ull : ((1ull << hb) - 1);
+        k_set_u64<<<1, 1, 0, a.st>>>(&rs->prefix, kmin & ~low);
+        int top = ((hb - 1) / 8) * 8;
+        for (int shift = top; shift >= 0; shift -= 8) {
+          k_range_hist<<<grid_for(na, 256, 4 * sms), 256, 0, a.st>>>(alist, na, sup, wl, rs, shift);
+          CK_LAUNCH();
+          k_range_select<<<1, 32, 0, a.st>>>(rs, shift, shift == 0);
+          CK_LAUNCH();
+        }
+        ull he[2];
+        CK(cudaMemcpyAsync(he, &rs->est, sizeof(he), cudaMemcpyDeviceToHost, a.st));
+        CK(cudaStreamSynchronize(a.st));
+        init_est = he[0];
+        thi = he[1];
+      }
+    } else {
+      k_set_u64<<<1, 1, 0, a.st>>>(&rs->theta_hi, thi);
+    }
+    CK_LAUNCH();
+    prev_init_est = init_est;
+    cur_final = 0;
+    // ---- snapshot + first active set (Alg. 4 l.6-9)
+    CK(cudaMemsetAsync(dc, 0, 4, a.st));
+    k_scan_frontier<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, sup, init, &rs->theta_hi, 1, front, dc);
+    CK_LAUNCH();
+    uint32_t nf = fetch(a, dc);
+    // ---- peeling rounds (Alg. 4 l.10-13)
+    while (nf > 0) {
+      rounds++;
+      CK(cudaMemsetAsync(dc + 1, 0, 6 * 4, a.st));
+      CK(cudaMemsetAsync(sumw, 0, 8, a.st));
+      PrepArgs R;
+      R.frontier = front;
+      R.nf = nf;
+      R.p_off = p_off;
+      R.p_adj = p_adj;
+      R.o_len = o_len;
+      R.part = part;
+      R.pi = pi;
+      R.ytouch = ytouch;
+      R.touched = touched;
+      R.touched_n = dc + 2;
+      R.compact = prm.compact;
+      R.sum_w = sumw;
+      R.lists = plists;
+      R.counts = dc + 3;
+      R.nx = nx;
+      R.small_ids = small_ids;
+      k_prep<<<grid_for((size_t)nf * 32, T, cap), T, 0, a.st>>>(R);
+      CK_LAUNCH();
+      unsigned hc[6];
+      ull hw;
+      CK(cudaMemcpyAsync(hc, dc + 1, sizeof(hc), cudaMemcpyDeviceToHost, a.st));
+      CK(cudaMemcpyAsync(&hw, sumw, 8, cudaMemcpyDeviceToHost, a.st));
+      CK(cudaStreamSynchronize(a.st));
+      cur_final += hw;
+      bool do_recount = prm.recount && hw > wbound;
+      if (do_recount) {
+        // Sec. 5.1: re-count the remaining vertices instead of peeling
+        recounts++;
+        k_mark_peeled<<<grid_for(nf, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab);
+        CK_LAUNCH();
+        CK(cudaMemsetAsync(cnt_lab, 0, (size_t)G.n * 8, a.st));
+        CountOut rc;
+        rc.cnt_lab = (uint64_t *)cnt_lab;
+        rc.lab_isU = isU;
+        rc.want_side = side;
+        rc.lab_alive = lab_alive;
+        rc.wedges = (uint64_t *)(dwedge + 1);
+        count_butterflies(a, G, rc);
+        k_gather_counts<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, x2lab, cnt_lab, sup);
+        CK_LAUNCH();
+      } else {
+        wedges_cd += hw;
+        PA.next = front2;
+        PA.next_n = dc + 1;
+        if (hc[2 + PC_WARP]) {
+          k_peel_warp<<<grid_for((size_t)hc[2 + PC_WARP] * 32, PWT, 6 * sms), PWT, wsm, a.st>>>(PA, plists + (size_t)PC_WARP * nx,
+                                                                                                dc + 3 + PC_WARP);
+          CK_LAUNCH();
+        }
+        if (hc[2 + PC_BDENSE]) {
+          k_peel_block<PC_BDENSE><<<std::min<unsigned>(hc[2 + PC_BDENSE], 2 * sms), PBT, peel_block_smem(PC_BDENSE), a.st>>>(
+              PA, plists + (size_t)PC_BDENSE * nx, dc + 3 + PC_BDENSE, nullptr);
+          CK_LAUNCH();
+        }
+        if (hc[2 + PC_BHASH]) {
+          k_peel_block<PC_BHASH><<<std::min<unsigned>(hc[2 + PC_BHASH], 2 * sms), PBT, peel_block_smem(PC_BHASH), a.st>>>(
+              PA, plists + (size_t)PC_BHASH * nx, dc + 3 + PC_BHASH, nullptr);
+          CK_LAUNCH();
+        }
+        if (hc[2 + PC_GLOBAL]) {
+          if (!gscr) gscr = a.zeros<uint32_t>((size_t)gscr_blocks * nx);
+          k_peel_block<PC_GLOBAL><<<std::min<unsigned>(hc[2 + PC_GLOBAL], gscr_blocks), PBT, peel_block_smem(PC_GLOBAL), a.st>>>(
+              PA, plists + (size_t)PC_GLOBAL * nx, dc + 3 + PC_GLOBAL, gscr);
+          CK_LAUNCH();
+        }
+        k_mark_peeled<<<grid_for(nf, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab);
+        CK_LAUNCH();
+      }
+      if (prm.compact && hc[1]) {
+        k_compact<<<grid_for((size_t)hc[1] * 32, T, cap), T, 0, a.st>>>(touched, dc + 2, o_off, o_adj, o_len, ytouch, state);
+        CK_LAUNCH();
+      }
+      if (do_recount) {
+        CK(cudaMemsetAsync(dc + 1, 0, 4, a.st));
+        k_scan_frontier<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, sup, init, &rs->theta_hi, 0, front2, dc + 1);
+        CK_LAUNCH();
+      }
+      nf = fetch(a, dc + 1);
+      std::swap(front, front2);
+    }
+    pi++;
+  }
+  uint32_t nparts = pi;
+  CK(cudaEventRecord(ev[2], a.st));
+
+  // ---- fine phase: partitions, induced subgraphs, LPT queue
+  uint32_t *pcnt = a.zeros<uint32_t>(nparts + 1), *ps = a.alloc<uint32_t>(nparts + 1);
+  k_part_hist<<<grid_for(nx, T, cap), T, 0, a.st>>>(part, nx, pcnt);
+  CK_LAUNCH();
+  exclusive_scan_u32(a, pcnt, ps, nparts);
+  uint32_t *xs = a.alloc<uint32_t>(nx), *loc = a.alloc<uint32_t>(nx);
+  {
+    uint64_t *key = a.alloc<uint64_t>(nx);
+    k_part_keys<<<grid_for(nx, T, cap), T, 0, a.st>>>(part, nx, key, xs);
+    CK_LAUNCH();
+    sort_pairs(a, key, xs, nx, bits_for(nparts));
+    a.free(key);
+  }
+  k_loc<<<grid_for(nx, T, cap), T, 0, a.st>>>(xs, nx, part, ps, loc, state);
+  CK_LAUNCH();
+  int bp = bits_for(nparts);
+  uint32_t *fd_adj = a.alloc<uint32_t>(G.m), *fd_part = a.alloc<uint32_t>(G.m);
+  {
+    uint64_t *key = a.alloc<uint64_t>(G.m);
+    k_fd_keys<<<grid_for((size_t)ny * 32, T, cap), T, 0, a.st>>>(o_off, o_adj0, ny, part, bp, key, fd_adj);
+    CK_LAUNCH();
+    sort_pairs(a, key, fd_adj, G.m, bits_for(ny) + bp);
+    a.free(key);
+  }
+  k_fd_part_of<<<grid_for(G.m, T, cap), T, 0, a.st>>>(fd_adj, G.m, part, fd_part);
+  CK_LAUNCH();
+  ull *work = a.zeros<ull>(nparts);
+  k_fd_work<<<grid_for((size_t)ny * 32, T, cap), T, 0, a.st>>>(o_off, ny, fd_part, work);
+  CK_LAUNCH();
+  std::vector<ull> hwork(nparts);
+  CK(cudaMemcpyAsync(hwork.data(), work, nparts * 8, cudaMemcpyDeviceToHost, a.st));
+  CK(cudaStreamSynchronize(a.st));
+  std::vector<uint32_t> ord(nparts);
+  for (uint32_t i = 0; i < nparts; i++) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return hwork[x] > hwork[y]; });
+  uint32_t *dord = a.alloc<uint32_t>(nparts);
+  CK(cudaMemcpyAsync(dord, ord.data(), nparts * 4, cudaMemcpyHostToDevice, a.st));
+  CK(cudaEventRecord(ev[3], a.st));
+
+  // support initialisation vector (Sec. 3.1.1) -> fine-phase supports
+  CK(cudaMemcpyAsync(sup, init, (size_t)nx * 8, cudaMemcpyDeviceToDevice, a.st));
+  FDArgs F;
+  F.p_off = p_off;
+  F.p_adj = p_adj;
+  F.o_off = o_off;
+  F.fd_adj = fd_adj;
+  F.fd_part = fd_part;
+  F.xs = xs;
+  F.ps = ps;
+  F.loc = loc;
+  F.order = dord;
+  F.nparts = nparts;
+  F.state = state;
+  F.sup = sup;
+  F.theta = (ull *)theta_out;
+  F.buf_a = alist;
+  F.buf_b = alist2;
+  F.buf_f = front;
+  F.buf_big = front2;
+  F.gcnt = a.zeros<uint32_t>(nx);
+  F.queue = dc + 8;
+  CK(cudaMemsetAsync(dc + 8, 0, 4, a.st));
+  F.wedges = dwedge + 2;
+  F.steps = dwedge + 3;
+  F.updates = dwedge + 4;
+  unsigned fgrid = std::min<unsigned>(nparts, sms);
+  k_fd_tip<<<fgrid, FT, fd_smem(), a.st>>>(F, fd_warp_bytes(), fd_dense_off());
+  CK_LAUNCH();
+  CK(cudaEventRecord(ev[4], a.st));
+  CK(cudaStreamSynchronize(a.st));
+  if (st) {
+    ull hd[5];
+    CK(cudaMemcpy(hd, dwedge, sizeof(hd), cudaMemcpyDeviceToHost));
+    float t01, t12, t23, t34;
+    cudaEventElapsedTime(&t01, ev[0], ev[1]);
+    cudaEventElapsedTime(&t12, ev[1], ev[2]);
+    cudaEventElapsedTime(&t23, ev[2], ev[3]);
+    cudaEventElapsedTime(&t34, ev[3], ev[4]);
+    st->wedges_count += hd[0];
+    st->wedges_cd += wedges_cd + hd[1];
+    st->wedges_fd += hd[2];
+    st->fd_steps += hd[3];
+    st->updates += hd[4];
+    st->rounds += rounds;
+    st->recounts += recounts;
+    st->wedge_bound = G.wedge_bound;
+    st->ns_count += (uint64_t)(t01 * 1e6);
+    st->ns_cd += (uint64_t)(t12 * 1e6);
+    st->ns_part += (uint64_t)(t23 * 1e6);
+    st->ns_fd += (uint64_t)(t34 * 1e6);
+    st->parts_used = nparts;
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+}
+
+}  // namespace pbng

@@ -1,0 +1,161 @@
+"""GPU parity: butterfly counts and tip numbers from the CUDA library against
+the CPU oracle, bit-exact, through the C ABI (via the thin binding)."""
+import numpy as np
+import pytest
+
+import bigraph_gen as gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pbng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_12511_gb300 import build as b
+    b.build()
+    import paper_2110_12511_gb300 as m
+    m.lib()
+    return m
+
+
+def rand_graph(nu, nv, p, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.random((nu, nv)) < p
+    eu, ev = np.nonzero(a)
+    return gen.from_edges(nu, nv, eu, ev)
+
+
+def graphs():
+    out = {
+        "gprime": gen.from_edges(4, 3, [0, 0, 1, 1, 1, 2, 2, 3, 3], [0, 1, 0, 1, 2, 1, 2, 1, 2]),
+        "k_5_7": gen.complete(5, 7),
+        "k_40_3": gen.complete(40, 3),
+        "rand_30_20": rand_graph(30, 20, 0.3, 1),
+        "rand_dense_60_50": rand_graph(60, 50, 0.7, 2),
+        "uniform_2k_1k_20k": gen.make("uniform_2k_1k_20k"),
+        "chunglu_20k_4k_200k": gen.make("chunglu_20k_4k_200k"),
+        "chunglu_5k_1k_50k_planted": gen.make("chunglu_5k_1k_50k_planted"),
+        "isolated": gen.from_edges(6, 5, [0, 0, 1, 1], [0, 1, 0, 1]),
+    }
+    return out
+
+
+GRAPHS = graphs()
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_counts_match_oracle(pbng, name):
+    g = GRAPHS[name]
+    dg = pbng.to_device(g)
+    cu, cv, ce = pbng.count(dg, vertices=True, edges=True)
+    assert np.array_equal(pbng.as_u64(cu), oracle.vertex_counts(g, "U"))
+    assert np.array_equal(pbng.as_u64(cv), oracle.vertex_counts(g, "V"))
+    assert np.array_equal(pbng.as_u64(ce), oracle.edge_counts(g))
+
+
+_tip_cache = {}
+
+
+def oracle_tip(name, side):
+    k = (name, side)
+    if k not in _tip_cache:
+        _tip_cache[k] = oracle.tip(GRAPHS[name], side)
+    return _tip_cache[k]
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("side", ["U", "V"])
+def test_tip_matches_oracle(pbng, name, side):
+    g = GRAPHS[name]
+    dg = pbng.to_device(g)
+    got = pbng.as_u64(pbng.tip_decompose(dg, side, P=8))
+    assert np.array_equal(got, oracle_tip(name, side))
+
+
+@pytest.mark.parametrize("P", [1, 2, 8, 150, 10 ** 6])
+@pytest.mark.parametrize("side", ["U", "V"])
+def test_tip_independent_of_P(pbng, P, side):
+    name = "chunglu_5k_1k_50k_planted"
+    dg = pbng.to_device(GRAPHS[name])
+    got = pbng.as_u64(pbng.tip_decompose(dg, side, P=P))
+    assert np.array_equal(got, oracle_tip(name, side))
+
+
+def test_uniform_config_tip_u_p8(pbng):
+    name = "uniform_2k_1k_20k"
+    dg = pbng.to_device(GRAPHS[name])
+    got, st = pbng.tip_decompose(dg, "U", P=8, with_stats=True)
+    assert np.array_equal(pbng.as_u64(got), oracle_tip(name, "U"))
+    assert 1 <= st["parts_used"] <= 8
+    assert st["rounds"] >= st["parts_used"]
+
+
+@pytest.mark.parametrize("recount,compact", [(False, False), (False, True), (True, False), (True, True)])
+def test_tip_optimisations_do_not_change_results(pbng, recount, compact):
+    name = "chunglu_20k_4k_200k"
+    dg = pbng.to_device(GRAPHS[name])
+    for side in ("U", "V"):
+        got = pbng.as_u64(pbng.tip_decompose(dg, side, P=40, recount=recount, compact=compact))
+        assert np.array_equal(got, oracle_tip(name, side))
+
+
+def test_tip_explicit_and_random_bounds(pbng):
+    name = "chunglu_20k_4k_200k"
+    g = GRAPHS[name]
+    dg = pbng.to_device(g)
+    want = oracle_tip(name, "U")
+    rng = np.random.default_rng(7)
+    for trial in range(4):
+        hi = int(want.max()) + 2
+        b = np.unique(rng.integers(1, hi, size=int(rng.integers(1, 30)))).astype(np.uint64)
+        got = pbng.as_u64(pbng.tip_decompose(dg, "U", P=len(b) + 1, bounds=b))
+        assert np.array_equal(got, want)
+    # bounds at the exact tip-number levels, and bounds far below the minimum
+    lv = np.unique(want)[1:].astype(np.uint64)
+    got = pbng.as_u64(pbng.tip_decompose(dg, "U", P=len(lv) + 1, bounds=lv))
+    assert np.array_equal(got, want)
+
+
+def test_tip_host_buffers(pbng):
+    name = "chunglu_5k_1k_50k_planted"
+    got = pbng.tip_decompose_host(GRAPHS[name], "V", P=20)
+    assert np.array_equal(got, oracle_tip(name, "V"))
+
+
+def test_batch_matches_individual(pbng):
+    gs = [gen.batch_graph(1000 + i, scale=0.05) for i in range(12)] + [GRAPHS["gprime"], GRAPHS["isolated"]]
+    dgs = [pbng.to_device(g) for g in gs]
+    res = pbng.tip_decompose_batch(dgs, "U", P=30)
+    for g, r in zip(gs, res):
+        assert np.array_equal(pbng.as_u64(r), oracle.tip(g, "U"))
+    res = pbng.tip_decompose_batch(dgs, "V", P=5)
+    for g, r in zip(gs, res):
+        assert np.array_equal(pbng.as_u64(r), oracle.tip(g, "V"))
+
+
+def test_empty_graphs(pbng):
+    import torch
+    g = gen.from_edges(3, 4, [], [])
+    dg = pbng.to_device(g)
+    assert (pbng.as_u64(pbng.tip_decompose(dg, "U", P=4)) == 0).all()
+    cu, cv, ce = pbng.count(dg, vertices=True, edges=True)
+    assert (pbng.as_u64(cu) == 0).all() and (pbng.as_u64(cv) == 0).all() and ce.numel() == 0
+
+
+def test_malformed_csr_is_rejected(pbng):
+    import torch
+    cases = {
+        "unsorted": ([0, 3, 4], [2, 0, 1, 1]),
+        "duplicate": ([0, 2, 3], [1, 1, 0]),
+        "out_of_range": ([0, 1, 2], [0, 9]),
+        "bad_offsets": ([0, 3, 2], [0, 1, 2]),
+    }
+    for name, (off, adj) in cases.items():
+        dg = pbng.DeviceGraph(2, 3, torch.tensor(off, dtype=torch.int64, device="cuda"),
+                              torch.tensor(adj, dtype=torch.int32, device="cuda"))
+        with pytest.raises(pbng.PbngError) as ei:
+            pbng.tip_decompose(dg, "U", P=2)
+        assert ei.value.code == pbng.PBNG_EINVAL, name
