@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 two-phase tip decomposition.
+
+One step = plain GPU two-phase tip decomposition (PBNG, Sec. 3.1-3.2) of BOTH
+vertex sides of the Chung-Lu power-law bipartite graph |U|=1M, |V|=200k,
+m=20M, degree exponents 2.1 (U) and 2.5 (V), degree cap 50k, P=150, with
+the graph resident in HBM.  Metric: wedges traversed per second (the
+paper's work unit, Tab. 4) over the whole job; ms_per_step is the
+decomposition time of both sides.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pbng|reference]
+
+N > 1 (one process per GPU under torch.distributed.run): every rank
+decomposes its own replica of the graph; there is no data-path collective.
+--impl reference times the CPU oracle (sequential bottom-up peeling,
+Alg. 2) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "chunglu_1m_200k_20m"
+WORKLOAD_DESC = ("plain GPU two-phase tip decomposition of both sides, Chung-Lu |U|=1M |V|=200k m=20M, "
+                 "exponents 2.1/2.5, degree cap 50k, P=150")
+# CPU-baseline sample: the same Chung-Lu recipe at 1/20 scale
+SAMPLE = dict(kind="chung_lu", nu=50000, nv=10000, m=1000000, gu=2.1, gv=2.5, dmax=5000, seed=22)
+SAMPLE_DESC = "oracle BUP tip decomposition of both sides of the same Chung-Lu recipe at 1/20 scale (|U|=50k |V|=10k m=1M)"
+SAMPLE_SMALL = dict(kind="chung_lu", nu=20000, nv=4000, m=200000, gu=2.1, gv=2.5, dmax=2000, seed=12)
+SAMPLE_SMALL_DESC = "oracle BUP tip decomposition of both sides of the same Chung-Lu recipe at 1/100 scale (|U|=20k |V|=4k m=200k)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2110_12511_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        if n.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(group):
+    """DRAM bytes per launch of a kernel group from the committed ncu summary,
+    or None when the kernel sources changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    sha = kernel_sources_sha()
+    for line in open(p):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == WORKLOAD and f[1] == group and f[2] == sha:
+            return float(f[3])
+    return None
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+        return self
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def tip_wedges(st):
+    return st["wedges_count"] + st["wedges_cd"] + st["wedges_fd"]
+
+
+def oracle_sample(spec, sides=("U", "V")):
+    """Time the oracle on a sample; returns (wedges, seconds).  The oracle's
+    tip BUP traverses sum_v d_v^2 wedges to count and the same again to peel."""
+    import bigraph_gen as gen
+    import oracle
+    g = gen.make(dict(spec))
+    du = np.diff(g.u_off).astype(np.float64)
+    dv = np.bincount(g.u_adj, minlength=g.nv).astype(np.float64)
+    t0 = time.perf_counter()
+    for s in sides:
+        oracle.tip(g, s)
+    dt = time.perf_counter() - t0
+    w = 0.0
+    for s in sides:
+        w += 2.0 * float((dv ** 2).sum() if s == "U" else (du ** 2).sum())
+    return w, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    spec, desc = (SAMPLE, SAMPLE_DESC) if args.steps + args.warmup <= 12 else (SAMPLE_SMALL, SAMPLE_SMALL_DESC)
+    for _ in range(args.warmup):
+        oracle_sample(spec)
+    tw, tt = 0.0, 0.0
+    for _ in range(args.steps):
+        w, dt = oracle_sample(spec)
+        tw += w
+        tt += dt
+    v = tw / tt
+    line = {"metric": "tip decomposition wedges/s (both sides)", "value": v, "unit": "wedges/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD_DESC, "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "wedges/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "wedges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pbng", choices=["pbng", "reference"])
+    ap.add_argument("--P", type=int, default=150)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD)
+    args = ap.parse_args()
+    ws, rank, local = dist_info()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import torch.distributed as dist
+    import bigraph_gen as gen
+    import paper_2110_12511_gb300 as pbng
+    from paper_2110_12511_gb300 import build as pbuild
+
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or ws == 1:
+        pbuild.build()
+    if ws > 1:
+        dist.barrier()
+    pbng.lib()
+
+    g = gen.make(args.workload)
+    dg = pbng.to_device(g, dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        su = pbng.tip_decompose(dg, "U", P=args.P, with_stats=True)[1]
+        sv = pbng.tip_decompose(dg, "V", P=args.P, with_stats=True)[1]
+        return su, sv
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region (device time per step; L2 flushed between steps)
+    stats = []
+    times = []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats.append(step())
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    ms_total = sum(times)
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    wedges_step = tip_wedges(stats[0][0]) + tip_wedges(stats[0][1])
+    value = ws * wedges_step * args.steps / (ms_max / 1000.0)
+
+    # ---- kernel roofline: dominant kernel group over the timed steps
+    groups = {"count": ("ns_k_count", "bytes_count", "n_k_count"), "peel": ("ns_k_peel", "bytes_peel", "n_k_peel"),
+              "fd": ("ns_k_fd", "bytes_fd", "n_k_fd")}
+    agg = {}
+    for k, (tn, bn, nn) in groups.items():
+        ns = sum(s[tn] for st in stats for s in st)
+        by = sum(s[bn] for st in stats for s in st)
+        nl = sum(s[nn] for st in stats for s in st)
+        agg[k] = (ns, by, nl)
+    dom = max(agg, key=lambda k: agg[k][0])
+    ns, by, nl = agg[dom]
+    peak, peak_kind = peaks()
+    achieved = by / ns if ns else 0.0  # bytes per ns == GB/s
+    tr = ncu_traffic(dom)
+    roofline = {"bound": "hbm", "kernel_group": dom, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": tr,
+                "launches": nl, "ms_per_launch": ns / 1e6 / max(nl, 1),
+                "groups": {k: {"ms": v[0] / 1e6, "GB": v[1] / 1e9, "launches": v[2],
+                               "GBps": (v[1] / v[0] if v[0] else 0.0)} for k, v in agg.items()}}
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside
+    pin_off = torch.from_numpy(np.ascontiguousarray(g.u_off).view(np.int64)).pin_memory()
+    pin_adj = torch.from_numpy(np.ascontiguousarray(g.u_adj).view(np.int32)).pin_memory()
+
+    class HostG:
+        nu, nv = g.nu, g.nv
+        u_off = pin_off.numpy().view(np.uint64)
+        u_adj = pin_adj.numpy().view(np.uint32)
+
+    hg = HostG()
+    pbng.tip_decompose_host(hg, "U", P=args.P)
+    e2e_t = []
+    e2e_w = 0
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, su = pbng.tip_decompose_host(hg, "U", P=args.P, with_stats=True)
+        _, sv = pbng.tip_decompose_host(hg, "V", P=args.P, with_stats=True)
+        e2e_t.append(time.perf_counter() - t0)
+        e2e_w += tip_wedges(su) + tip_wedges(sv)
+    tt = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_value = ws * e2e_w / float(tt.item())
+    h2d = 2 * ((g.nu + 1) * 8 + g.m * 4)
+    d2h = (g.nu + g.nv) * 8
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            w, dt = oracle_sample(SAMPLE)
+            cpu = {"value": w / dt, "unit": "wedges/s", "cores": 1, "kind": "oracle", "sample": SAMPLE_DESC,
+                   "seconds": dt}
+        s0u, s0v = stats[0]
+        line = {
+            "metric": "tip decomposition wedges/s (both sides)", "value": value, "unit": "wedges/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded Chung-Lu generator)",
+            "config": {"workload": WORKLOAD_DESC, "name": args.workload, "P": args.P, "sides": "U,V",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "flushed between steps (256 MB write)", "nu": g.nu, "nv": g.nv, "m": g.m,
+                       "wedges_per_step": wedges_step,
+                       "rounds_u": s0u["rounds"], "rounds_v": s0v["rounds"], "recounts_u": s0u["recounts"],
+                       "recounts_v": s0v["recounts"], "parts_u": s0u["parts_used"], "parts_v": s0v["parts_used"],
+                       "phase_ms_u": {k: s0u["ns_" + k] / 1e6 for k in ("setup", "count", "cd", "part", "fd", "total")},
+                       "phase_ms_v": {k: s0v["ns_" + k] / 1e6 for k in ("setup", "count", "cd", "part", "fd", "total")}},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "wedges/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": 1000 * sum(e2e_t) / len(e2e_t)},
+            "gpu_launches": int(sum(s["launches"] for st in stats for s in st)),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -89,6 +89,15 @@ typedef struct pbng_stats {
   uint64_t ns_setup, ns_count, ns_cd, ns_part, ns_fd, ns_total;
   uint32_t parts_used;     /* non-empty coarse partitions */
   uint32_t reserved;
+  /* kernel-level measurements (CUDA events bracketing the launches of each
+     kernel group on the call's stream) and the algorithmic bytes those
+     launches must move: 4 B per wedge traversed, 12 B per (vertex, middle
+     vertex) expansion, 16 B per 64-bit support update, 8 B per frontier
+     entity; wing: 8 B per bloom-edge link, 16 B per update, 8 B per bloom */
+  uint64_t launches;       /* kernels launched by the call */
+  uint64_t ns_k_count, ns_k_peel, ns_k_fd;     /* counting / coarse peel / fine peel kernels */
+  uint64_t bytes_count, bytes_peel, bytes_fd;  /* algorithmic bytes of those kernels */
+  uint64_t n_k_count, n_k_peel, n_k_fd;        /* launches in each group */
 } pbng_stats;
 
 /* Fill *o with the defaults listed above. */

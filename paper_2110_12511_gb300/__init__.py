@@ -42,7 +42,9 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "wedges_count", "wedges_cd", "wedges_fd", "updates", "links", "blooms", "rounds", "recounts", "fd_steps",
         "wedge_bound", "ns_setup", "ns_count", "ns_cd", "ns_part", "ns_fd", "ns_total")] + [
-        ("parts_used", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+        ("parts_used", ctypes.c_uint32), ("reserved", ctypes.c_uint32)] + [(n, ctypes.c_uint64) for n in (
+        "launches", "ns_k_count", "ns_k_peel", "ns_k_fd", "bytes_count", "bytes_peel", "bytes_fd",
+        "n_k_count", "n_k_peel", "n_k_fd")]
 
     def to_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}

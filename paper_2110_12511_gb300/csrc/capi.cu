@@ -107,6 +107,34 @@ TipParams tip_params(uint32_t P, const pbng_opts &o) {
   return p;
 }
 
+// Turn on kernel-span profiling for a call that asked for statistics.
+struct ProfScope {
+  pbng_stats *st;
+  uint64_t l0;
+  ProfScope(pbng_stats *s, cudaStream_t stream) : st(s), l0(g_launches) {
+    g_prof = Prof();
+    g_prof.on = s != nullptr;
+    g_prof.st = stream;
+  }
+  void fill() {
+    if (!st) return;
+    uint64_t ns[PROF_NGROUPS];
+    g_prof.collect(ns);
+    st->launches = g_launches - l0;
+    st->ns_k_count = ns[PROF_COUNT];
+    st->ns_k_peel = ns[PROF_PEEL];
+    st->ns_k_fd = ns[PROF_FD];
+    st->n_k_count = g_prof.launches[PROF_COUNT];
+    st->n_k_peel = g_prof.launches[PROF_PEEL];
+    st->n_k_fd = g_prof.launches[PROF_FD];
+  }
+  ~ProfScope() {
+    uint64_t ns[PROF_NGROUPS];
+    g_prof.collect(ns);
+    g_prof.on = false;
+  }
+};
+
 struct Timer {
   cudaEvent_t a, b;
   cudaStream_t st;
@@ -168,6 +196,7 @@ int pbng_count(const pbng_bigraph *g, uint64_t *out_u, uint64_t *out_v, uint64_t
     check_graph(g);
     init_device_pool();
     Arena a((cudaStream_t)o.stream);
+    ProfScope ps(stats, a.st);
     Timer tm(a.st);
     pbng_bigraph d = device_graph(a, g, o.mem);
     Graph G;
@@ -178,7 +207,7 @@ int pbng_count(const pbng_bigraph *g, uint64_t *out_u, uint64_t *out_v, uint64_t
     be.init(a, out_e, G.m, o.mem);
     uint64_t *cnt = a.zeros<uint64_t>((size_t)G.n + 1);
     if (be.dev && G.m) CK(cudaMemsetAsync(be.dev, 0, (size_t)G.m * 8, a.st));
-    uint64_t *wd = a.zeros<uint64_t>(1);
+    uint64_t *wd = a.zeros<uint64_t>(3);
     CountOut co;
     co.cnt_lab = cnt;
     co.cnt_e = be.dev;
@@ -192,13 +221,17 @@ int pbng_count(const pbng_bigraph *g, uint64_t *out_u, uint64_t *out_v, uint64_t
     bu.finish(a);
     bv.finish(a);
     be.finish(a);
-    uint64_t w = fetch(a, wd);
+    uint64_t w[3];
+    CK(cudaMemcpyAsync(w, wd, sizeof(w), cudaMemcpyDeviceToHost, a.st));
     CK(cudaStreamSynchronize(a.st));
     if (stats) {
       memset(stats, 0, sizeof(*stats));
-      stats->wedges_count = w;
+      stats->wedges_count = w[0];
+      stats->updates = w[2];
+      stats->bytes_count = 4 * w[0] + 12 * w[1] + 16 * w[2];
       stats->wedge_bound = G.wedge_bound;
       stats->ns_total = tm.ns();
+      ps.fill();
     }
   });
 }
@@ -213,6 +246,7 @@ int pbng_tip_decompose(const pbng_bigraph *g, pbng_side side, uint32_t P, uint64
     check_graph(g);
     init_device_pool();
     Arena a((cudaStream_t)o.stream);
+    ProfScope ps(stats, a.st);
     Timer tm(a.st);
     pbng_bigraph d = device_graph(a, g, o.mem);
     Graph G;
@@ -233,6 +267,7 @@ int pbng_tip_decompose(const pbng_bigraph *g, pbng_side side, uint32_t P, uint64
       *stats = st;
       stats->ns_setup = t_setup;
       stats->ns_total = tm.ns();
+      ps.fill();
     }
   });
 }
@@ -245,6 +280,7 @@ int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, c
     check_graph(g);
     init_device_pool();
     Arena a((cudaStream_t)o.stream);
+    ProfScope ps(stats, a.st);
     Timer tm(a.st);
     pbng_bigraph d = device_graph(a, g, o.mem);
     Graph G;
@@ -262,6 +298,7 @@ int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, c
       *stats = st;
       stats->ns_setup = t_setup;
       stats->ns_total = tm.ns();
+      ps.fill();
     }
   });
 }
@@ -310,6 +347,7 @@ extern "C" int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng
     TipParams p = tip_params(P, o);
     init_device_pool();
     Arena a((cudaStream_t)o.stream);
+    ProfScope ps(stats, a.st);
     Timer tm(a.st);
     std::vector<BatchDesc> hd(n);
     uint64_t nu = 0, nv = 0, m = 0;
@@ -389,6 +427,7 @@ extern "C" int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng
     if (stats) {
       *stats = st;
       stats->ns_total = tm.ns();
+      ps.fill();
     }
   });
 }

@@ -38,7 +38,7 @@ struct CArgs {
   unsigned long long *cnt, *cnt_e;
   const uint8_t *alive, *isU;
   int want_side;
-  unsigned long long *wedges;
+  unsigned long long *ctr;  // [0] wedges, [1] (start, mid) expansions, [2] support updates
 };
 
 __device__ __forceinline__ bool want(const CArgs &A, uint32_t x) {
@@ -88,7 +88,8 @@ struct HashPolicy {
   __device__ void inc(uint32_t k) const { h.inc(k); }
   __device__ uint32_t get(uint32_t k) const { return h.get(k); }
   template <class Grp, int N>
-  __device__ uint64_t drain(const CArgs &A, uint32_t, uint32_t, uint32_t, bool sl, const Grp &g, MidBuf<N> &) const {
+  __device__ uint64_t drain(const CArgs &A, uint32_t, uint32_t, uint32_t, bool sl, const Grp &g, MidBuf<N> &,
+                            uint64_t &nat) const {
     uint64_t ss = 0;
     for (uint32_t i = g.rank(); i < cap; i += N) {
       uint32_t k = h.key[i];
@@ -96,7 +97,7 @@ struct HashPolicy {
         uint32_t c = h.val[i];
         if (c >= 2) {
           uint64_t bc = choose2(c);
-          if (sl) atomicAdd(&A.cnt[k], (unsigned long long)bc);
+          if (sl) atomicAdd(&A.cnt[k], (unsigned long long)bc), nat++;
           ss += bc;
         }
         h.key[i] = EMPTY_KEY;
@@ -112,14 +113,15 @@ struct DensePolicy {  // counters for labels [0, s) in shared memory
   __device__ void inc(uint32_t k) const { atomicAdd(&c[k], 1u); }
   __device__ uint32_t get(uint32_t k) const { return c[k]; }
   template <class Grp, int N>
-  __device__ uint64_t drain(const CArgs &A, uint32_t s, uint32_t, uint32_t, bool sl, const Grp &g, MidBuf<N> &) const {
+  __device__ uint64_t drain(const CArgs &A, uint32_t s, uint32_t, uint32_t, bool sl, const Grp &g, MidBuf<N> &,
+                            uint64_t &nat) const {
     uint64_t ss = 0;
     for (uint32_t i = g.rank(); i < s; i += N) {
       uint32_t x = c[i];
       if (x) {
         if (x >= 2) {
           uint64_t bc = choose2(x);
-          if (sl) atomicAdd(&A.cnt[i], (unsigned long long)bc);
+          if (sl) atomicAdd(&A.cnt[i], (unsigned long long)bc), nat++;
           ss += bc;
         }
         c[i] = 0;
@@ -135,7 +137,7 @@ struct GlobalPolicy {  // per-block dense counters over all labels in global mem
   __device__ uint32_t get(uint32_t k) const { return __ldcg(&c[k]); }
   template <class Grp, int N>
   __device__ uint64_t drain(const CArgs &A, uint32_t s, uint32_t so, uint32_t sd, bool sl, const Grp &g,
-                            MidBuf<N> &mb) const {
+                            MidBuf<N> &mb, uint64_t &nat) const {
     uint64_t ss = 0;
     for (uint32_t base = 0; base < sd; base += N) {
       uint32_t T = load_mids(A, s, so, sd, base, g, mb);
@@ -144,7 +146,7 @@ struct GlobalPolicy {  // per-block dense counters over all labels in global mem
         uint32_t x = atomicExch(&c[last], 0u);  // first visitor of last takes its count
         if (x >= 2) {
           uint64_t bc = choose2(x);
-          if (sl) atomicAdd(&A.cnt[last], (unsigned long long)bc);
+          if (sl) atomicAdd(&A.cnt[last], (unsigned long long)bc), nat++;
           ss += bc;
         }
       });
@@ -159,7 +161,7 @@ __device__ void count_start(const CArgs &A, uint32_t s, const Grp &g, MidBuf<N> 
   uint32_t so = A.off[s], sd = A.off[s + 1] - so;
   bool sl = want(A, s);
   bool md = A.want_side < 0 || !sl;
-  uint64_t wc = 0;
+  uint64_t wc = 0, nat = 0;
   // pass 1: wedge_count[last]++ for every valid wedge (Alg. 1 l.9-13)
   for (uint32_t base = 0; base < sd; base += N) {
     uint32_t T = load_mids(A, s, so, sd, base, g, mb);
@@ -180,27 +182,31 @@ __device__ void count_start(const CArgs &A, uint32_t s, const Grp &g, MidBuf<N> 
         uint32_t c = tbl.get(last);
         if (c >= 2) {
           atomicAdd(&mb.acc[i], (unsigned long long)(c - 1));
-          if (A.cnt_e) atomicAdd(&A.cnt_e[A.eid[pos]], (unsigned long long)(c - 1));
+          if (A.cnt_e) atomicAdd(&A.cnt_e[A.eid[pos]], (unsigned long long)(c - 1)), nat++;
         }
       });
       g.sync();
       int r = g.rank();
       unsigned long long x = mb.acc[r];
       if (x && base + r < sd) {
-        if (md) atomicAdd(&A.cnt[mb.mid[r]], x);
-        if (A.cnt_e) atomicAdd(&A.cnt_e[A.eid[so + base + r]], x);
+        if (md) atomicAdd(&A.cnt[mb.mid[r]], x), nat++;
+        if (A.cnt_e) atomicAdd(&A.cnt_e[A.eid[so + base + r]], x), nat++;
       }
       mb.acc[r] = 0;
       g.sync();
     }
   }
   // pass 3: start and last gain C(wc, 2) (Alg. 1 l.15-17); clears the table
-  uint64_t ss = tbl.drain(A, s, so, sd, sl, g, mb);
+  uint64_t ss = tbl.drain(A, s, so, sd, sl, g, mb, nat);
   g.sync();
-  uint64_t tot = g.sum64(ss), wt = g.sum64(wc);
+  uint64_t tot = g.sum64(ss), wt = g.sum64(wc), at = g.sum64(nat);
   if (g.rank() == 0) {
-    if (sl && tot) atomicAdd(&A.cnt[s], (unsigned long long)tot);
-    if (A.wedges && wt) atomicAdd(A.wedges, (unsigned long long)wt);
+    if (sl && tot) atomicAdd(&A.cnt[s], (unsigned long long)tot), at++;
+    if (A.ctr) {
+      if (wt) atomicAdd(&A.ctr[0], (unsigned long long)wt);
+      atomicAdd(&A.ctr[1], (unsigned long long)sd);
+      if (at) atomicAdd(&A.ctr[2], (unsigned long long)at);
+    }
   }
   g.sync();
 }
@@ -310,7 +316,7 @@ void count_butterflies(Arena &a, const Graph &G, const CountOut &o) {
   A.alive = o.lab_alive;
   A.isU = o.lab_isU;
   A.want_side = o.want_side;
-  A.wedges = (unsigned long long *)o.wedges;
+  A.ctr = (unsigned long long *)o.wedges;
   if (o.cnt_e && !G.lab_eid) fail(PBNG_EINVAL, "internal: edge ids missing for per-edge counts");
 
   static bool attr = false;
@@ -329,6 +335,7 @@ void count_butterflies(Arena &a, const Graph &G, const CountOut &o) {
   CK(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, a.st));
   CK(cudaStreamSynchronize(a.st));
 
+  g_prof.begin(PROF_COUNT);
   if (hc[C_WARP]) {
     size_t smem = (WT / 32) * align16(WARP_CAP * 8 + sizeof(MidBuf<32>));
     static bool wa = false;
@@ -356,7 +363,10 @@ void count_butterflies(Arena &a, const Graph &G, const CountOut &o) {
     k_count_block<C_GLOBAL><<<grid, BT, block_smem(C_GLOBAL), a.st>>>(A, lists + (size_t)C_GLOBAL * G.n,
                                                                        counts + C_GLOBAL, scr);
     CK_LAUNCH();
+    g_prof.end();
     a.free(scr);
+  } else {
+    g_prof.end();
   }
   a.free(lists);
   a.free(counts);

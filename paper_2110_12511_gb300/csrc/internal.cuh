@@ -16,7 +16,31 @@ struct Error {
 [[noreturn]] void fail(int code, const char *fmt, ...);
 void cuda_check(cudaError_t e, const char *what, const char *file, int line);
 #define CK(x) ::pbng::cuda_check((x), #x, __FILE__, __LINE__)
-#define CK_LAUNCH() ::pbng::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+#define CK_LAUNCH() (::pbng::g_launches++, ::pbng::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__))
+extern thread_local uint64_t g_launches;
+
+// ------------------------------------------------------------- profiling
+// Event spans around groups of kernel launches, collected when a caller
+// asks for statistics.
+enum { PROF_COUNT = 0, PROF_PEEL = 1, PROF_FD = 2, PROF_NGROUPS = 3 };
+struct Prof {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  struct Span {
+    cudaEvent_t a, b;
+    int group;
+  };
+  std::vector<Span> spans;
+  uint64_t launches[PROF_NGROUPS] = {0, 0, 0};
+  uint64_t bytes[PROF_NGROUPS] = {0, 0, 0};
+  uint64_t l0 = 0;
+  int cur = -1;
+  void begin(int group);
+  void end();
+  // sum the spans per group (synchronises on the last event) and reset
+  void collect(uint64_t ns[PROF_NGROUPS]);
+};
+extern thread_local Prof g_prof;
 
 // -------------------------------------------------------------- allocation
 // Per-call arena of stream-ordered allocations, released when the call ends.
@@ -105,7 +129,7 @@ struct CountOut {
   const uint8_t *lab_alive = nullptr;  // restrict to alive labels (null = all)
   const uint8_t *lab_isU = nullptr;    // side of each label (needed when want_side >= 0)
   int want_side = -1;            // -1 both; 0 only U labels' counts; 1 only V labels'
-  uint64_t *wedges = nullptr;    // device counter of traversed wedges (optional)
+  uint64_t *wedges = nullptr;    // optional device counters [3]: wedges, expansions, updates
 };
 // Alg. 1 over the labelled adjacency (all starts).
 void count_butterflies(Arena &a, const Graph &G, const CountOut &o);

@@ -10,6 +10,41 @@ namespace pbng {
 
 // ------------------------------------------------------------------ errors
 thread_local char g_detail[512];
+thread_local uint64_t g_launches = 0;
+thread_local Prof g_prof;
+
+// --------------------------------------------------------------- profiling
+void Prof::begin(int group) {
+  if (!on) return;
+  Span s;
+  s.group = group;
+  cudaEventCreate(&s.a);
+  cudaEventCreate(&s.b);
+  cudaEventRecord(s.a, st);
+  spans.push_back(s);
+  cur = group;
+  l0 = g_launches;
+}
+
+void Prof::end() {
+  if (!on || cur < 0) return;
+  cudaEventRecord(spans.back().b, st);
+  launches[cur] += g_launches - l0;
+  cur = -1;
+}
+
+void Prof::collect(uint64_t ns[PROF_NGROUPS]) {
+  for (int i = 0; i < PROF_NGROUPS; i++) ns[i] = 0;
+  if (!spans.empty()) cudaEventSynchronize(spans.back().b);
+  for (auto &s : spans) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) ns[s.group] += (uint64_t)((double)ms * 1e6);
+    cudaEventDestroy(s.a);
+    cudaEventDestroy(s.b);
+  }
+  cudaGetLastError();
+  spans.clear();
+}
 
 void fail(int code, const char *fmt, ...) {
   va_list ap;

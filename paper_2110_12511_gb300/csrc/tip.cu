@@ -224,7 +224,7 @@ struct PrepArgs {
   uint32_t *ytouch, *touched;
   unsigned *touched_n;
   int compact;
-  ull *sum_w;
+  ull *sum_w;  // [0] wedges of the active set, [1] its (vertex, mid) expansions
   uint64_t *lists;  // PNCLASS x nx
   unsigned *counts;
   uint32_t nx;
@@ -251,7 +251,8 @@ __global__ void k_prep(PrepArgs A) {
     for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
     if (lane == 0) {
       A.part[x] = A.pi;
-      atomicAdd(A.sum_w, (ull)W);
+      atomicAdd(&A.sum_w[0], (ull)W);
+      atomicAdd(&A.sum_w[1], (ull)xd);
       if (W >= 2) {
         int c = W <= PW_MAXW ? PC_WARP : (A.small_ids ? PC_BDENSE : (W <= PB_MAXW ? PC_BHASH : PC_GLOBAL));
         unsigned p = atomicAdd(&A.counts[c], 1u);
@@ -723,7 +724,9 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   CK(cudaEventRecord(ev[0], a.st));
 
   // ---- initial supports by Alg. 1 (counts of the peeled side only)
-  ull *dwedge = a.zeros<ull>(8);  // [0] count, [1] recount, [2] fd wedges, [3] fd steps, [4] updates
+  // [0..2] initial count (wedges, expansions, updates), [3..5] re-counts,
+  // [6] fd wedges, [7] fd steps, [8] coarse updates, [9] fine updates
+  ull *dwedge = a.zeros<ull>(16);
   uint8_t *isU = label_sides(a, G);
   ull *cnt_lab = a.zeros<ull>(G.n);
   CountOut co;
@@ -759,6 +762,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   // small device counters: [0] frontier size, [1] next size, [2] touched, [3..6] class counts, [7] alist size
   unsigned *dc = a.zeros<unsigned>(16);
   ull *sumw = a.zeros<ull>(2);
+  uint64_t exp_cd = 0, front_cd = 0;
   RangeState *rs = a.zeros<RangeState>(1);
   ull *wl = a.alloc<ull>(nx);
   uint32_t *gscr = nullptr;  // per-block dense counters for the heaviest vertices
@@ -774,7 +778,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   PA.state = state;
   PA.sup = sup;
   PA.theta_hi = &rs->theta_hi;
-  PA.updates = dwedge + 4;
+  PA.updates = dwedge + 8;
   PA.nx = nx;
 
   static bool attr = false;
@@ -872,7 +876,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     while (nf > 0) {
       rounds++;
       CK(cudaMemsetAsync(dc + 1, 0, 6 * 4, a.st));
-      CK(cudaMemsetAsync(sumw, 0, 8, a.st));
+      CK(cudaMemsetAsync(sumw, 0, 16, a.st));
       PrepArgs R;
       R.frontier = front;
       R.nf = nf;
@@ -893,10 +897,11 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       k_prep<<<grid_for((size_t)nf * 32, T, cap), T, 0, a.st>>>(R);
       CK_LAUNCH();
       unsigned hc[6];
-      ull hw;
+      ull hw2[2];
       CK(cudaMemcpyAsync(hc, dc + 1, sizeof(hc), cudaMemcpyDeviceToHost, a.st));
-      CK(cudaMemcpyAsync(&hw, sumw, 8, cudaMemcpyDeviceToHost, a.st));
+      CK(cudaMemcpyAsync(hw2, sumw, 16, cudaMemcpyDeviceToHost, a.st));
       CK(cudaStreamSynchronize(a.st));
+      ull hw = hw2[0];
       cur_final += hw;
       bool do_recount = prm.recount && hw > wbound;
       if (do_recount) {
@@ -910,13 +915,16 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
         rc.lab_isU = isU;
         rc.want_side = side;
         rc.lab_alive = lab_alive;
-        rc.wedges = (uint64_t *)(dwedge + 1);
+        rc.wedges = (uint64_t *)(dwedge + 3);
         count_butterflies(a, G, rc);
         k_gather_counts<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, x2lab, cnt_lab, sup);
         CK_LAUNCH();
       } else {
         wedges_cd += hw;
+        exp_cd += hw2[1];
+        front_cd += nf;
         PA.next = front2;
+        g_prof.begin(PROF_PEEL);
         PA.next_n = dc + 1;
         if (hc[2 + PC_WARP]) {
           k_peel_warp<<<grid_for((size_t)hc[2 + PC_WARP] * 32, PWT, 6 * sms), PWT, wsm, a.st>>>(PA, plists + (size_t)PC_WARP * nx,
@@ -939,6 +947,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
               PA, plists + (size_t)PC_GLOBAL * nx, dc + 3 + PC_GLOBAL, gscr);
           CK_LAUNCH();
         }
+        g_prof.end();
         k_mark_peeled<<<grid_for(nf, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab);
         CK_LAUNCH();
       }
@@ -1021,16 +1030,18 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   F.gcnt = a.zeros<uint32_t>(nx);
   F.queue = dc + 8;
   CK(cudaMemsetAsync(dc + 8, 0, 4, a.st));
-  F.wedges = dwedge + 2;
-  F.steps = dwedge + 3;
-  F.updates = dwedge + 4;
+  F.wedges = dwedge + 6;
+  F.steps = dwedge + 7;
+  F.updates = dwedge + 9;
   unsigned fgrid = std::min<unsigned>(nparts, sms);
+  g_prof.begin(PROF_FD);
   k_fd_tip<<<fgrid, FT, fd_smem(), a.st>>>(F, fd_warp_bytes(), fd_dense_off());
   CK_LAUNCH();
+  g_prof.end();
   CK(cudaEventRecord(ev[4], a.st));
   CK(cudaStreamSynchronize(a.st));
   if (st) {
-    ull hd[5];
+    ull hd[10];
     CK(cudaMemcpy(hd, dwedge, sizeof(hd), cudaMemcpyDeviceToHost));
     float t01, t12, t23, t34;
     cudaEventElapsedTime(&t01, ev[0], ev[1]);
@@ -1038,10 +1049,14 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     cudaEventElapsedTime(&t23, ev[2], ev[3]);
     cudaEventElapsedTime(&t34, ev[3], ev[4]);
     st->wedges_count += hd[0];
-    st->wedges_cd += wedges_cd + hd[1];
-    st->wedges_fd += hd[2];
-    st->fd_steps += hd[3];
-    st->updates += hd[4];
+    st->wedges_cd += wedges_cd + hd[3];
+    st->wedges_fd += hd[6];
+    st->fd_steps += hd[7];
+    st->updates += hd[8] + hd[9];
+    // algorithmic bytes (per-unit figures documented in pbng.h)
+    st->bytes_count += 4 * (hd[0] + hd[3]) + 12 * (hd[1] + hd[4]) + 16 * (hd[2] + hd[5]);
+    st->bytes_peel += 4 * wedges_cd + 12 * exp_cd + 16 * hd[8] + 8 * front_cd;
+    st->bytes_fd += 4 * hd[6] + 12 * (uint64_t)G.m + 16 * hd[9] + 8 * (uint64_t)nx;
     st->rounds += rounds;
     st->recounts += recounts;
     st->wedge_bound = G.wedge_bound;
