@@ -177,7 +177,7 @@ CONFIGS = {
 
 def make(name_or_spec) -> Graph:
     """Generate a named workload (see ``CONFIGS``) or an explicit spec dict."""
-    spec = CONFIGS[name_or_spec] if isinstance(name_or_spec, str) else dict(name_or_spec)
+    spec = dict(CONFIGS[name_or_spec]) if isinstance(name_or_spec, str) else dict(name_or_spec)
     kind = spec.pop("kind") if "kind" in spec else "chung_lu"
     if kind == "uniform":
         return uniform(spec["nu"], spec["nv"], spec["m"], spec["seed"])

@@ -136,6 +136,34 @@ int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, c
 int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng_side side, uint32_t P,
                              uint64_t *const *outs, const pbng_opts *opts, pbng_stats *stats);
 
+/* Per-vertex butterfly counts of the U side, computed WITHOUT ANY DEVICE
+ * ALLOCATION.  The paper has no counterpart: this is an access path for
+ * callers that cannot allocate device memory, such as code that must stay
+ * inside a fixed, pre-reserved memory budget or whose device memory is owned
+ * by another framework's allocator.  out_u[u] = sum over u' != u of
+ * C(|N_u cap N_u'|, 2), the same values pbng_count() writes to out_u.
+ * Both CSRs are supplied by the caller: u_off/u_adj as for pbng_bigraph and
+ * v_off/v_adj (nv+1 offsets, m ids in [0,nu)) the transpose of it; pass the
+ * two swapped to count the V side.  Offsets and ids are range-checked;
+ * a v-side CSR that is in range but not the transpose gives unspecified
+ * counts.  All pointers are device pointers; the call synchronises `stream`
+ * (a cudaStream_t, NULL = legacy default stream).
+ * Scratch: one fixed 64 MiB array in device global memory, declared in the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  It limits nu to 16,777,216; a larger nu is rejected with
+ * PBNG_EINVAL before any device work.  Every call on a device shares that
+ * array and finds the previous call's contents in it (each call clears the
+ * part it uses first), so calls that overlap on the GPU, for example on two
+ * streams at once, race and give wrong counts.  The first call on each
+ * device looks up the array's device address with cudaGetSymbolAddress
+ * while that device is current; make that first call before any stream
+ * capture.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  Status codes as for the other calls; pbng_last_error_detail()
+ * names the cause of a failure. */
+int pbng_vertex_counts_noalloc(uint32_t nu, uint32_t nv, uint64_t m, const uint64_t *u_off,
+                               const uint32_t *u_adj, const uint64_t *v_off, const uint32_t *v_adj,
+                               uint64_t *out_u, void *stream);
+
 /* Name of a status code. */
 const char *pbng_strerror(int status);
 /* Detail of the most recent failure on this thread ("" if none). */

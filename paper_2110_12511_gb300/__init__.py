@@ -92,6 +92,8 @@ def lib():
         L.pbng_last_error_detail.restype = ctypes.c_char_p
         L.pbng_version.argtypes = []
         L.pbng_version.restype = C
+        L.pbng_vertex_counts_noalloc.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, P, P, P, P, P, P]
+        L.pbng_vertex_counts_noalloc.restype = C
         _lib = L
     return _lib
 
@@ -243,3 +245,18 @@ def tip_decompose_batch(dgs, side="U", P=150, stream=None, with_stats=False, **k
     _check(rc, "pbng_tip_decompose_batch")
     res = [t[:(d.nu if s == SIDE_U else d.nv)] for t, d in zip(outs, dgs)]
     return (res, st.to_dict()) if with_stats else res
+
+
+def vertex_counts_noalloc(dg: DeviceGraph, dg_t: DeviceGraph, stream=None):
+    """Per-vertex butterfly counts of dg's U side without any device
+    allocation by the library (fixed static scratch; see include/pbng.h).
+    ``dg_t`` is the transposed graph (its U-side CSR is dg's V-side CSR)."""
+    import torch
+    out = torch.empty(max(dg.nu, 1), dtype=torch.int64, device=dg.u_off.device)
+    s = stream if stream is not None else torch.cuda.current_stream(dg.u_off.device)
+    rc = lib().pbng_vertex_counts_noalloc(dg.nu, dg.nv, dg.m, dg.u_off.data_ptr(),
+                                          dg.u_adj.data_ptr() if dg.m else None, dg_t.u_off.data_ptr(),
+                                          dg_t.u_adj.data_ptr() if dg_t.m else None, out.data_ptr(),
+                                          ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "pbng_vertex_counts_noalloc")
+    return out[:dg.nu]
