@@ -31,11 +31,15 @@ namespace {
 
 enum : uint8_t { ST_ALIVE = 0, ST_ACTIVE = 1, ST_PEELED = 2 };
 
-constexpr uint32_t PW_MAXW = 256, PW_CAP = 512;    // warp-per-vertex, shared hash
-constexpr uint32_t PB_MAXW = 4096, PB_CAP = 8192;  // block-per-vertex, shared hash
-constexpr uint32_t P_DENSE = 16384;                // dense shared counters when ids < this
+constexpr uint32_t PW_MAXW = 256, PW_CAP = 512;  // warp-per-vertex, shared hash
+constexpr uint32_t PB_CAP = 8192;                // block-per-vertex shared hash slots (64 KB)
+constexpr uint32_t PB_FILL = PB_CAP / 2;         // most distinct targets a hash pass may hold
+constexpr uint32_t P_CHUNK = 2 * PB_CAP;         // block-per-vertex dense counters (same 64 KB)
+constexpr int PB_PER_SM = 3;                     // resident blocks per SM (shared memory bound)
+constexpr uint32_t P_DENSE = 16384;              // fine phase: dense shared counters when |X_p| <= this
 constexpr int PBT = 512, PWT = 256;
-enum { PC_WARP = 0, PC_BDENSE = 1, PC_BHASH = 2, PC_GLOBAL = 3, PNCLASS = 4 };
+enum { PC_WARP = 0, PC_BLOCK = 1, PNCLASS = 2 };
+static_assert(P_CHUNK <= 2 * PB_CAP, "dense counters share the hash table memory");
 
 using ull = unsigned long long;
 
@@ -99,7 +103,7 @@ struct PHash {
       uint32_t k = h.key[i];
       if (k != EMPTY_KEY) {
         uint32_t c = h.val[i];
-        if (c >= 2) {
+        if (c >= 2 && A.state[k] == ST_ALIVE) {  // active and peeled targets get nothing
           dec_support(A, k, choose2(c), thi);
           nup++;
         }
@@ -111,40 +115,162 @@ struct PHash {
   }
 };
 
-struct PDense {  // dense counters indexed by vertex id (shared or global memory)
-  uint32_t *c;
-  __device__ void inc(uint32_t k) const { atomicAdd(&c[k], 1u); }
-  template <class Grp, int N>
-  __device__ uint64_t drain(const PeelArgs &A, uint32_t xo, uint32_t xd, const Grp &g, PMid<N> &mb, uint64_t thi) const {
-    uint64_t nup = 0;
-    for (uint32_t base = 0; base < xd; base += N) {
-      uint32_t T = peel_load(A, xo, xd, base, g, mb);
-      peel_walk(A, g, mb, T, [&](uint32_t xp) {
-        if (A.state[xp] != ST_ALIVE) return;
-        uint32_t x = atomicExch(&c[xp], 0u);
-        if (x >= 2) {
-          dec_support(A, xp, choose2(x), thi);
-          nup++;
-        }
-      });
-      g.sync();
-    }
-    return nup;
-  }
-};
-
 template <class Grp, int N, class Tbl>
 __device__ void peel_vertex(const PeelArgs &A, uint32_t x, const Grp &g, PMid<N> &mb, const Tbl &tbl, uint64_t thi) {
   uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
   for (uint32_t base = 0; base < xd; base += N) {
     uint32_t T = peel_load(A, xo, xd, base, g, mb);
-    peel_walk(A, g, mb, T, [&](uint32_t xp) {
-      if (A.state[xp] == ST_ALIVE) tbl.inc(xp);
-    });
+    peel_walk(A, g, mb, T, [&](uint32_t xp) { tbl.inc(xp); });
     g.sync();
   }
   uint64_t nup = tbl.drain(A, xo, xd, g, mb, thi);
   g.sync();
+  uint64_t t = g.sum64(nup);
+  if (g.rank() == 0 && t && A.updates) atomicAdd(A.updates, (ull)t);
+}
+
+// Slice of y's current list holding target ids in [c0, c1) (lists are sorted).
+template <int N>
+__device__ __forceinline__ uint32_t chunk_load(const PeelArgs &A, uint32_t xo, uint32_t xd, uint32_t base, uint32_t c0,
+                                               uint32_t c1, bool full, const BlockGrp<N> &g, PMid<N> &mb) {
+  int r = g.rank();
+  uint32_t lo = 0, len = 0;
+  if (base + r < xd) {
+    uint32_t y = A.p_adj[xo + base + r];
+    uint32_t s0 = A.o_off[y], L = A.o_len[y];
+    if (full) {
+      lo = s0;
+      len = L;
+    } else {
+      uint32_t a0 = lower_bound_u32(A.o_adj + s0, L, c0);
+      uint32_t a1 = a0 + lower_bound_u32(A.o_adj + s0 + a0, L - a0, c1);
+      lo = s0 + a0;
+      len = a1 - a0;
+    }
+  }
+  mb.lo[r] = lo;
+  return g.scan(len, mb.pre);
+}
+
+// Shared hash whose keys are stored as id + 1, so that an all-zero table is
+// empty and the same memory can serve as zeroed dense counters.
+struct ZHash {
+  uint32_t *key, *val;
+  uint32_t mask;
+  __device__ __forceinline__ void inc(uint32_t id) const {
+    uint32_t k = id + 1, h = hash32(id) & mask;
+    volatile uint32_t *vk = key;
+    for (;;) {
+      uint32_t cur = vk[h];
+      if (cur == k) break;
+      if (cur == 0) {
+        uint32_t prev = atomicCAS(&key[h], 0u, k);
+        if (prev == 0 || prev == k) break;
+      }
+      h = (h + 1) & mask;
+    }
+    atomicAdd(&val[h], 1u);
+  }
+};
+
+// Block per active vertex.  The target id range [0, nx) is covered by
+// consecutive ranges [c0, c1); for each range the slices of the current
+// lists holding targets in it are found by binary search (lists are sorted)
+// and its wedges are aggregated per target in 64 KB of shared memory:
+//  - dense counters when the range is at most 16K ids wide,
+//  - else an open-addressing hash when its wedges (which bound its distinct
+//    targets) fit at load 1/2; a range that would overflow is halved first.
+// The first range width is chosen from the vertex's wedge count W so that a
+// typical range fills the hash, and widths adapt to the observed density.
+// Each aggregated target x' that is still unpeeled loses C(c(x,x'), 2).
+template <int N>
+__device__ void peel_vertex_block(const PeelArgs &A, uint32_t x, uint32_t W, const BlockGrp<N> &g, PMid<N> &mb,
+                                  uint32_t *tab, uint64_t thi) {
+  uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
+  uint64_t nup = 0;
+  uint32_t width;
+  if (A.nx <= P_CHUNK || W <= PB_FILL) width = A.nx;
+  else width = (uint32_t)max((uint64_t)P_CHUNK, (uint64_t)A.nx * PB_FILL / W);
+  uint32_t c0 = 0;
+  while (c0 < A.nx) {
+    uint32_t c1 = (uint32_t)min((uint64_t)A.nx, (uint64_t)c0 + width);
+    bool full = c0 == 0 && c1 == A.nx;
+    bool dense = c1 - c0 <= P_CHUNK;
+    // wedges of the range; for xd > N only an upper bound is needed to pick
+    // the table, so sum the slice lengths chunk by chunk
+    uint32_t T = 0;
+    for (uint32_t base = 0; base < xd; base += N) T += chunk_load(A, xo, xd, base, c0, c1, full, g, mb);
+    if (T == 0) {
+      c0 = c1;
+      if (width < A.nx / 2) width *= 2;
+      continue;
+    }
+    if (!dense && T > PB_FILL) {  // too many targets for the hash: halve the range
+      width = max(P_CHUNK, (c1 - c0) / 2);
+      continue;
+    }
+    uint32_t *key = tab, *val = tab + PB_CAP;
+    uint32_t cap = dense ? 0 : pow2_at_least(max(2u * T, 64u));
+    ZHash h{key, val, cap - 1};
+    auto inc = [&](uint32_t xp) {
+      if (dense) atomicAdd(&tab[xp - c0], 1u);
+      else h.inc(xp);
+    };
+    auto take = [&](uint32_t xp) {
+      uint32_t c = atomicExch(&tab[xp - c0], 0u);
+      if (c >= 2 && A.state[xp] == ST_ALIVE) {
+        dec_support(A, xp, choose2(c), thi);
+        nup++;
+      }
+    };
+    if (xd <= (uint32_t)N) {
+      peel_walk(A, g, mb, T, inc);  // the single slice load is still in mb
+    } else {
+      for (uint32_t base = 0; base < xd; base += N) {
+        uint32_t Tb = chunk_load(A, xo, xd, base, c0, c1, full, g, mb);
+        peel_walk(A, g, mb, Tb, inc);
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+    if (!dense) {  // drain the hash slot by slot
+      for (uint32_t i = g.rank(); i < cap; i += N) {
+        uint32_t k = key[i];
+        if (k) {
+          uint32_t c = val[i], xp = k - 1;
+          if (c >= 2 && A.state[xp] == ST_ALIVE) {
+            dec_support(A, xp, choose2(c), thi);
+            nup++;
+          }
+          key[i] = 0;
+          val[i] = 0;
+        }
+      }
+    } else if (T >= (c1 - c0) / 2) {  // dense and crowded: scan the counters
+      for (uint32_t i = g.rank(); i < c1 - c0; i += N) {
+        uint32_t c = tab[i];
+        if (c) {
+          tab[i] = 0;
+          uint32_t xp = c0 + i;
+          if (c >= 2 && A.state[xp] == ST_ALIVE) {
+            dec_support(A, xp, choose2(c), thi);
+            nup++;
+          }
+        }
+      }
+    } else if (xd <= (uint32_t)N) {  // dense and sparse: walk the wedges again
+      peel_walk(A, g, mb, T, take);
+    } else {
+      for (uint32_t base = 0; base < xd; base += N) {
+        uint32_t Tb = chunk_load(A, xo, xd, base, c0, c1, full, g, mb);
+        peel_walk(A, g, mb, Tb, take);
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+    c0 = c1;
+    if (T < PB_FILL / 4 && width < A.nx / 2) width *= 2;
+  }
   uint64_t t = g.sum64(nup);
   if (g.rank() == 0 && t && A.updates) atomicAdd(A.updates, (ull)t);
 }
@@ -169,50 +295,25 @@ __global__ void __launch_bounds__(PWT) k_peel_warp(PeelArgs A, const uint64_t *l
   }
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(PBT) k_peel_block(PeelArgs A, const uint64_t *list, const unsigned *count,
-                                                     uint32_t *gscratch) {
+__global__ void __launch_bounds__(PBT) k_peel_block(PeelArgs A, const uint64_t *list, const unsigned *count) {
   extern __shared__ __align__(16) uint8_t sm[];
   PMid<PBT> &mb = *(PMid<PBT> *)sm;
   constexpr size_t o1 = align16(sizeof(PMid<PBT>));
   uint32_t *ws = (uint32_t *)(sm + o1);
   ull *ws64 = (ull *)(sm + o1 + 128);
-  uint8_t *tb = sm + o1 + 256;
+  uint32_t *tab = (uint32_t *)(sm + o1 + 256);  // PB_CAP keys + PB_CAP values, or P_CHUNK counters
   BlockGrp<PBT> g{ws, ws64};
-  if (KIND == PC_BDENSE) {
-    uint32_t *c = (uint32_t *)tb;
-    for (uint32_t i = threadIdx.x; i < P_DENSE; i += PBT) c[i] = 0;
-  } else if (KIND == PC_BHASH) {
-    uint32_t *key = (uint32_t *)tb;
-    for (uint32_t i = threadIdx.x; i < PB_CAP; i += PBT) key[i] = EMPTY_KEY, key[PB_CAP + i] = 0;
-  }
+  for (uint32_t i = threadIdx.x; i < 2 * PB_CAP; i += PBT) tab[i] = 0;  // empty hash == zero counters
   __syncthreads();
   uint64_t thi = *A.theta_hi;
   unsigned n = *count;
   for (size_t it = blockIdx.x; it < n; it += gridDim.x) {
     uint64_t item = list[it];
-    uint32_t x = (uint32_t)item, W = (uint32_t)(item >> 32);
-    if (KIND == PC_BDENSE) {
-      PDense p{(uint32_t *)tb};
-      peel_vertex(A, x, g, mb, p, thi);
-    } else if (KIND == PC_BHASH) {
-      uint32_t cap = pow2_at_least(max(2u * W, 64u));
-      uint32_t *key = (uint32_t *)tb;
-      PHash p{SmemHash{key, key + PB_CAP, cap - 1}, cap};
-      peel_vertex(A, x, g, mb, p, thi);
-    } else {
-      PDense p{gscratch + (size_t)blockIdx.x * A.nx};
-      peel_vertex(A, x, g, mb, p, thi);
-    }
+    peel_vertex_block(A, (uint32_t)item, (uint32_t)(item >> 32), g, mb, tab, thi);
   }
 }
 
-size_t peel_block_smem(int kind) {
-  size_t s = align16(sizeof(PMid<PBT>)) + 256;
-  if (kind == PC_BDENSE) s += P_DENSE * 4;
-  if (kind == PC_BHASH) s += PB_CAP * 8;
-  return s;
-}
+size_t peel_block_smem() { return align16(sizeof(PMid<PBT>)) + 256 + (size_t)PB_CAP * 8; }
 
 // ------------------------------------------------------- round bookkeeping
 struct PrepArgs {
@@ -221,14 +322,10 @@ struct PrepArgs {
   const uint32_t *p_off, *p_adj, *o_len;
   uint32_t *part;
   uint32_t pi;
-  uint32_t *ytouch, *touched;
-  unsigned *touched_n;
-  int compact;
   ull *sum_w;  // [0] wedges of the active set, [1] its (vertex, mid) expansions
   uint64_t *lists;  // PNCLASS x nx
   unsigned *counts;
   uint32_t nx;
-  int small_ids;    // nx <= P_DENSE
 };
 
 // one warp per active vertex: partition id, wedge count, class, touched Y lists
@@ -239,14 +336,7 @@ __global__ void k_prep(PrepArgs A) {
     uint32_t x = A.frontier[j];
     uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
     uint64_t W = 0;
-    for (uint32_t k = lane; k < xd; k += 32) {
-      uint32_t y = A.p_adj[xo + k];
-      W += A.o_len[y];
-      if (A.compact && atomicExch(&A.ytouch[y], 1u) == 0u) {
-        unsigned p = atomicAdd(A.touched_n, 1u);
-        A.touched[p] = y;
-      }
-    }
+    for (uint32_t k = lane; k < xd; k += 32) W += A.o_len[A.p_adj[xo + k]];
 #pragma unroll
     for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
     if (lane == 0) {
@@ -254,7 +344,7 @@ __global__ void k_prep(PrepArgs A) {
       atomicAdd(&A.sum_w[0], (ull)W);
       atomicAdd(&A.sum_w[1], (ull)xd);
       if (W >= 2) {
-        int c = W <= PW_MAXW ? PC_WARP : (A.small_ids ? PC_BDENSE : (W <= PB_MAXW ? PC_BHASH : PC_GLOBAL));
+        int c = W <= PW_MAXW ? PC_WARP : PC_BLOCK;
         unsigned p = atomicAdd(&A.counts[c], 1u);
         A.lists[(size_t)c * A.nx + p] = (uint64_t)x | ((uint64_t)min(W, (uint64_t)0xffffffffu) << 32);
       }
@@ -262,17 +352,37 @@ __global__ void k_prep(PrepArgs A) {
   }
 }
 
-__global__ void k_mark_peeled(const uint32_t *f, uint32_t nf, uint8_t *state, uint8_t *lab_alive, const uint32_t *x2lab) {
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < nf; j += (size_t)gridDim.x * blockDim.x) {
+// warp per peeled vertex: mark it, and count the dead entries it leaves in
+// the Y-side lists; a list is queued for compaction (dynamic graph update,
+// Sec. 5.2) once a quarter of it is dead, so each entry is scanned O(1) times
+// by compaction overall.
+__global__ void k_mark_peeled(const uint32_t *f, uint32_t nf, uint8_t *state, uint8_t *lab_alive, const uint32_t *x2lab,
+                              const uint32_t *p_off, const uint32_t *p_adj, const uint32_t *o_len, uint32_t *dead,
+                              uint32_t *ytouch, uint32_t *touched, unsigned *touched_n, int compact) {
+  int lane = threadIdx.x & 31;
+  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t j = gw; j < nf; j += nw) {
     uint32_t x = f[j];
-    state[x] = ST_PEELED;
-    if (lab_alive) lab_alive[x2lab[x]] = 0;
+    if (lane == 0) {
+      state[x] = ST_PEELED;
+      if (lab_alive) lab_alive[x2lab[x]] = 0;
+    }
+    if (!compact) continue;
+    uint32_t xo = p_off[x], xd = p_off[x + 1] - xo;
+    for (uint32_t k = lane; k < xd; k += 32) {
+      uint32_t y = p_adj[xo + k];
+      uint32_t d = atomicAdd(&dead[y], 1u) + 1;
+      if (4 * d >= o_len[y] && atomicExch(&ytouch[y], 1u) == 0u) {
+        unsigned p = atomicAdd(touched_n, 1u);
+        touched[p] = y;
+      }
+    }
   }
 }
 
 // warp per touched Y vertex: stable in-place removal of peeled X entries
 __global__ void k_compact(const uint32_t *touched, const unsigned *tn, const uint32_t *o_off, uint32_t *o_adj, uint32_t *o_len,
-                          uint32_t *ytouch, const uint8_t *state) {
+                          uint32_t *ytouch, uint32_t *dead, const uint8_t *state) {
   int lane = threadIdx.x & 31;
   size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
   unsigned n = *tn;
@@ -295,6 +405,7 @@ __global__ void k_compact(const uint32_t *touched, const unsigned *tn, const uin
     if (lane == 0) {
       o_len[y] = out;
       ytouch[y] = 0;
+      dead[y] = 0;
     }
   }
 }
@@ -756,7 +867,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   CK(cudaMemcpyAsync(o_adj, o_adj0, (size_t)G.m * 4, cudaMemcpyDeviceToDevice, a.st));
   k_degrees<<<grid_for(ny, T, cap), T, 0, a.st>>>(o_off, ny, o_len);
   CK_LAUNCH();
-  uint32_t *ytouch = a.zeros<uint32_t>(ny + 1), *touched = a.alloc<uint32_t>(ny + 1);
+  uint32_t *ytouch = a.zeros<uint32_t>(ny + 1), *touched = a.alloc<uint32_t>(ny + 1), *dead = a.zeros<uint32_t>(ny + 1);
   uint32_t *front = a.alloc<uint32_t>(nx), *front2 = a.alloc<uint32_t>(nx);
   uint64_t *plists = a.alloc<uint64_t>((size_t)PNCLASS * nx);
   // small device counters: [0] frontier size, [1] next size, [2] touched, [3..6] class counts, [7] alist size
@@ -765,9 +876,6 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   uint64_t exp_cd = 0, front_cd = 0;
   RangeState *rs = a.zeros<RangeState>(1);
   ull *wl = a.alloc<ull>(nx);
-  uint32_t *gscr = nullptr;  // per-block dense counters for the heaviest vertices
-  unsigned gscr_blocks = 2 * sms;
-  bool small_ids = nx <= P_DENSE;
 
   PeelArgs PA;
   PA.p_off = p_off;
@@ -785,9 +893,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   size_t wsm = (PWT / 32) * align16(PW_CAP * 8 + sizeof(PMid<32>));
   if (!attr) {
     CK(cudaFuncSetAttribute(k_peel_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
-    CK(cudaFuncSetAttribute(k_peel_block<PC_BDENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)peel_block_smem(PC_BDENSE)));
-    CK(cudaFuncSetAttribute(k_peel_block<PC_BHASH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)peel_block_smem(PC_BHASH)));
-    CK(cudaFuncSetAttribute(k_peel_block<PC_GLOBAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)peel_block_smem(PC_GLOBAL)));
+    CK(cudaFuncSetAttribute(k_peel_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)peel_block_smem()));
     CK(cudaFuncSetAttribute(k_fd_tip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fd_smem()));
     attr = true;
   }
@@ -885,15 +991,10 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       R.o_len = o_len;
       R.part = part;
       R.pi = pi;
-      R.ytouch = ytouch;
-      R.touched = touched;
-      R.touched_n = dc + 2;
-      R.compact = prm.compact;
       R.sum_w = sumw;
       R.lists = plists;
       R.counts = dc + 3;
       R.nx = nx;
-      R.small_ids = small_ids;
       k_prep<<<grid_for((size_t)nf * 32, T, cap), T, 0, a.st>>>(R);
       CK_LAUNCH();
       unsigned hc[6];
@@ -907,7 +1008,8 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       if (do_recount) {
         // Sec. 5.1: re-count the remaining vertices instead of peeling
         recounts++;
-        k_mark_peeled<<<grid_for(nf, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab);
+        k_mark_peeled<<<grid_for((size_t)nf * 32, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab, p_off, p_adj,
+                                                                          o_len, dead, ytouch, touched, dc + 2, prm.compact);
         CK_LAUNCH();
         CK(cudaMemsetAsync(cnt_lab, 0, (size_t)G.n * 8, a.st));
         CountOut rc;
@@ -931,28 +1033,18 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
                                                                                                 dc + 3 + PC_WARP);
           CK_LAUNCH();
         }
-        if (hc[2 + PC_BDENSE]) {
-          k_peel_block<PC_BDENSE><<<std::min<unsigned>(hc[2 + PC_BDENSE], 2 * sms), PBT, peel_block_smem(PC_BDENSE), a.st>>>(
-              PA, plists + (size_t)PC_BDENSE * nx, dc + 3 + PC_BDENSE, nullptr);
-          CK_LAUNCH();
-        }
-        if (hc[2 + PC_BHASH]) {
-          k_peel_block<PC_BHASH><<<std::min<unsigned>(hc[2 + PC_BHASH], 2 * sms), PBT, peel_block_smem(PC_BHASH), a.st>>>(
-              PA, plists + (size_t)PC_BHASH * nx, dc + 3 + PC_BHASH, nullptr);
-          CK_LAUNCH();
-        }
-        if (hc[2 + PC_GLOBAL]) {
-          if (!gscr) gscr = a.zeros<uint32_t>((size_t)gscr_blocks * nx);
-          k_peel_block<PC_GLOBAL><<<std::min<unsigned>(hc[2 + PC_GLOBAL], gscr_blocks), PBT, peel_block_smem(PC_GLOBAL), a.st>>>(
-              PA, plists + (size_t)PC_GLOBAL * nx, dc + 3 + PC_GLOBAL, gscr);
+        if (hc[2 + PC_BLOCK]) {
+          k_peel_block<<<std::min<unsigned>(hc[2 + PC_BLOCK], PB_PER_SM * sms), PBT, peel_block_smem(), a.st>>>(
+              PA, plists + (size_t)PC_BLOCK * nx, dc + 3 + PC_BLOCK);
           CK_LAUNCH();
         }
         g_prof.end();
-        k_mark_peeled<<<grid_for(nf, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab);
+        k_mark_peeled<<<grid_for((size_t)nf * 32, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab, p_off, p_adj,
+                                                                          o_len, dead, ytouch, touched, dc + 2, prm.compact);
         CK_LAUNCH();
       }
-      if (prm.compact && hc[1]) {
-        k_compact<<<grid_for((size_t)hc[1] * 32, T, cap), T, 0, a.st>>>(touched, dc + 2, o_off, o_adj, o_len, ytouch, state);
+      if (prm.compact) {
+        k_compact<<<4 * sms, T, 0, a.st>>>(touched, dc + 2, o_off, o_adj, o_len, ytouch, dead, state);
         CK_LAUNCH();
       }
       if (do_recount) {
