@@ -39,6 +39,7 @@ struct CArgs {
   const uint8_t *alive, *isU;
   int want_side;
   unsigned long long *ctr;  // [0] wedges, [1] (start, mid) expansions, [2] support updates
+  unsigned long long *be_nb, *be_np;  // per start: blooms (lasts with wc >= 2) and their twin pairs
 };
 
 __device__ __forceinline__ bool want(const CArgs &A, uint32_t x) {
@@ -89,7 +90,7 @@ struct HashPolicy {
   __device__ uint32_t get(uint32_t k) const { return h.get(k); }
   template <class Grp, int N>
   __device__ uint64_t drain(const CArgs &A, uint32_t, uint32_t, uint32_t, bool sl, const Grp &g, MidBuf<N> &,
-                            uint64_t &nat) const {
+                            uint64_t &nat, uint64_t &nb, uint64_t &np) const {
     uint64_t ss = 0;
     for (uint32_t i = g.rank(); i < cap; i += N) {
       uint32_t k = h.key[i];
@@ -99,6 +100,8 @@ struct HashPolicy {
           uint64_t bc = choose2(c);
           if (sl) atomicAdd(&A.cnt[k], (unsigned long long)bc), nat++;
           ss += bc;
+          nb++;
+          np += c;
         }
         h.key[i] = EMPTY_KEY;
         h.val[i] = 0;
@@ -114,7 +117,7 @@ struct DensePolicy {  // counters for labels [0, s) in shared memory
   __device__ uint32_t get(uint32_t k) const { return c[k]; }
   template <class Grp, int N>
   __device__ uint64_t drain(const CArgs &A, uint32_t s, uint32_t, uint32_t, bool sl, const Grp &g, MidBuf<N> &,
-                            uint64_t &nat) const {
+                            uint64_t &nat, uint64_t &nb, uint64_t &np) const {
     uint64_t ss = 0;
     for (uint32_t i = g.rank(); i < s; i += N) {
       uint32_t x = c[i];
@@ -123,6 +126,8 @@ struct DensePolicy {  // counters for labels [0, s) in shared memory
           uint64_t bc = choose2(x);
           if (sl) atomicAdd(&A.cnt[i], (unsigned long long)bc), nat++;
           ss += bc;
+          nb++;
+          np += x;
         }
         c[i] = 0;
       }
@@ -137,7 +142,7 @@ struct GlobalPolicy {  // per-block dense counters over all labels in global mem
   __device__ uint32_t get(uint32_t k) const { return __ldcg(&c[k]); }
   template <class Grp, int N>
   __device__ uint64_t drain(const CArgs &A, uint32_t s, uint32_t so, uint32_t sd, bool sl, const Grp &g,
-                            MidBuf<N> &mb, uint64_t &nat) const {
+                            MidBuf<N> &mb, uint64_t &nat, uint64_t &nb, uint64_t &np) const {
     uint64_t ss = 0;
     for (uint32_t base = 0; base < sd; base += N) {
       uint32_t T = load_mids(A, s, so, sd, base, g, mb);
@@ -148,6 +153,8 @@ struct GlobalPolicy {  // per-block dense counters over all labels in global mem
           uint64_t bc = choose2(x);
           if (sl) atomicAdd(&A.cnt[last], (unsigned long long)bc), nat++;
           ss += bc;
+          nb++;
+          np += x;
         }
       });
       g.sync();
@@ -197,9 +204,17 @@ __device__ void count_start(const CArgs &A, uint32_t s, const Grp &g, MidBuf<N> 
     }
   }
   // pass 3: start and last gain C(wc, 2) (Alg. 1 l.15-17); clears the table
-  uint64_t ss = tbl.drain(A, s, so, sd, sl, g, mb, nat);
+  uint64_t nb = 0, np = 0;
+  uint64_t ss = tbl.drain(A, s, so, sd, sl, g, mb, nat, nb, np);
   g.sync();
   uint64_t tot = g.sum64(ss), wt = g.sum64(wc), at = g.sum64(nat);
+  if (A.be_nb) {
+    uint64_t tb = g.sum64(nb), tp = g.sum64(np);
+    if (g.rank() == 0) {
+      A.be_nb[s] = tb;
+      A.be_np[s] = tp;
+    }
+  }
   if (g.rank() == 0) {
     if (sl && tot) atomicAdd(&A.cnt[s], (unsigned long long)tot), at++;
     if (A.ctr) {
@@ -317,6 +332,8 @@ void count_butterflies(Arena &a, const Graph &G, const CountOut &o) {
   A.isU = o.lab_isU;
   A.want_side = o.want_side;
   A.ctr = (unsigned long long *)o.wedges;
+  A.be_nb = (unsigned long long *)o.be_nb;
+  A.be_np = (unsigned long long *)o.be_np;
   if (o.cnt_e && !G.lab_eid) fail(PBNG_EINVAL, "internal: edge ids missing for per-edge counts");
 
   static bool attr = false;

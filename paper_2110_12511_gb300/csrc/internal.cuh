@@ -130,12 +130,27 @@ struct CountOut {
   const uint8_t *lab_isU = nullptr;    // side of each label (needed when want_side >= 0)
   int want_side = -1;            // -1 both; 0 only U labels' counts; 1 only V labels'
   uint64_t *wedges = nullptr;    // optional device counters [3]: wedges, expansions, updates
+  uint64_t *be_nb = nullptr;     // optional per-label BE-Index sizes: blooms started at the label
+  uint64_t *be_np = nullptr;     // and their twin pairs (caller zeroes both)
 };
 // Alg. 1 over the labelled adjacency (all starts).
 void count_butterflies(Arena &a, const Graph &G, const CountOut &o);
 
 // side flags of labels: isU[label] = 1 if the label is a U vertex
 uint8_t *label_sides(Arena &a, const Graph &G);
+
+// ------------------------------------------------------------ find_range
+struct RangeState {  // device-side state of the weighted selection
+  unsigned long long kmin, kmax, wsum;  // key range and total work of the remaining entities
+  unsigned long long prefix, below, tgt, est, theta_hi;
+  unsigned long long hist[256];
+};
+void set_u64(Arena &a, uint64_t *p, uint64_t v);
+// theta_hi for the remaining entities alist[0..na) with supports sup[] and
+// work wl[j] (aligned with alist): 1 + smallest K with work(sup <= K) >= tgt.
+// Leaves theta_hi in rs->theta_hi; *est = work(sup <= K).  Synchronises.
+uint64_t range_select(Arena &a, RangeState *rs, const uint32_t *alist, uint32_t na, const uint64_t *sup, const uint64_t *wl,
+                      uint64_t kmin, uint64_t kmax, uint64_t tgt, uint64_t *est);
 
 // ------------------------------------------------------------------ tip
 struct TipParams {

@@ -322,6 +322,7 @@ struct PrepArgs {
   const uint32_t *p_off, *p_adj, *o_len;
   uint32_t *part;
   uint32_t pi;
+  uint8_t *state;
   ull *sum_w;  // [0] wedges of the active set, [1] its (vertex, mid) expansions
   uint64_t *lists;  // PNCLASS x nx
   unsigned *counts;
@@ -341,6 +342,7 @@ __global__ void k_prep(PrepArgs A) {
     for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
     if (lane == 0) {
       A.part[x] = A.pi;
+      A.state[x] = ST_ACTIVE;  // active vertices receive no updates
       atomicAdd(&A.sum_w[0], (ull)W);
       atomicAdd(&A.sum_w[1], (ull)xd);
       if (W >= 2) {
@@ -425,12 +427,6 @@ __global__ void k_compact_list(const uint32_t *in, uint32_t n, const uint8_t *st
   }
 }
 
-struct RangeState {  // device-side state of find_range
-  ull kmin, kmax, wsum;  // filled by k_weights
-  ull prefix, below, tgt, est, theta_hi;
-  ull hist[256];
-};
-
 // warp per remaining vertex: work proxy w = wedges of x on the current graph
 // (Sec. 3.2), key range and total work
 __global__ void k_weights(const uint32_t *alist, uint32_t na, const uint32_t *p_off, const uint32_t *p_adj,
@@ -459,47 +455,6 @@ __global__ void k_weights(const uint32_t *alist, uint32_t na, const uint32_t *p_
     if (ws) atomicAdd(&rs->wsum, ws);
   }
 }
-
-// histogram of work by the digit at `shift` among keys matching the prefix
-__global__ void k_range_hist(const uint32_t *alist, uint32_t na, const ull *sup, const ull *wl, RangeState *rs, int shift) {
-  __shared__ ull h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  ull prefix = rs->prefix;
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < na; j += (size_t)gridDim.x * blockDim.x) {
-    ull key = sup[alist[j]];
-    if (shift + 8 >= 64 || ((key ^ prefix) >> (shift + 8)) == 0) {
-      ull w = wl[j];
-      if (w) atomicAdd(&h[(key >> shift) & 255u], w);
-    }
-  }
-  __syncthreads();
-  if (h[threadIdx.x]) atomicAdd(&rs->hist[threadIdx.x], h[threadIdx.x]);
-}
-
-// choose the digit where the cumulative work first reaches the target
-__global__ void k_range_select(RangeState *rs, int shift, int last) {
-  if (threadIdx.x != 0) return;
-  ull cum = rs->below;
-  int d = 255;
-  for (int i = 0; i < 256; i++) {
-    if (cum + rs->hist[i] >= rs->tgt) {
-      d = i;
-      break;
-    }
-    cum += rs->hist[i];
-  }
-  ull est = cum + rs->hist[d];
-  rs->below = cum;
-  rs->prefix = (rs->prefix & ~(255ull << shift)) | ((ull)d << shift);
-  for (int i = 0; i < 256; i++) rs->hist[i] = 0;
-  if (last) {
-    rs->est = est;
-    rs->theta_hi = rs->prefix + 1;
-  }
-}
-
-__global__ void k_set_u64(ull *p, ull v) { *p = v; }
 
 // start of a range (snapshot = 1): init <- support; any pass: the active set
 // is every unpeeled vertex with support below theta_hi
@@ -918,7 +873,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     // ---- range [theta(i), theta(i+1)) (Alg. 4 l.8, Sec. 3.1.3)
     bool last = pi + 1 >= P;
     CK(cudaMemsetAsync(rs, 0, sizeof(RangeState), a.st));
-    k_set_u64<<<1, 1, 0, a.st>>>(&rs->kmin, ~0ull);
+    set_u64(a, (uint64_t *)&rs->kmin, ~0ull);
     k_weights<<<grid_for((size_t)na * 32, T, cap), T, 0, a.st>>>(alist, na, p_off, p_adj, o_len, sup, wl, rs);
     CK_LAUNCH();
     ull hk[3];
@@ -946,31 +901,15 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       if (wsum == 0 || kmin == kmax) {
         thi = kmin + 1;
         init_est = wsum;
-        k_set_u64<<<1, 1, 0, a.st>>>(&rs->theta_hi, thi);
+        set_u64(a, (uint64_t *)&rs->theta_hi, thi);
       } else {
         double t = (double)wsum * scale / (double)(P - pi);
         ull tgt = t < 1.0 ? 1 : (t >= (double)wsum ? wsum : (ull)t);
-        k_set_u64<<<1, 1, 0, a.st>>>(&rs->tgt, tgt);
-        int hb = 64 - __builtin_clzll(kmin ^ kmax);  // low bits in which keys differ
-        ull low = hb >= 64 ? ~0ull : ((1ull << hb) - 1);
-        k_set_u64<<<1, 1, 0, a.st>>>(&rs->prefix, kmin & ~low);
-        int top = ((hb - 1) / 8) * 8;
-        for (int shift = top; shift >= 0; shift -= 8) {
-          k_range_hist<<<grid_for(na, 256, 4 * sms), 256, 0, a.st>>>(alist, na, sup, wl, rs, shift);
-          CK_LAUNCH();
-          k_range_select<<<1, 32, 0, a.st>>>(rs, shift, shift == 0);
-          CK_LAUNCH();
-        }
-        ull he[2];
-        CK(cudaMemcpyAsync(he, &rs->est, sizeof(he), cudaMemcpyDeviceToHost, a.st));
-        CK(cudaStreamSynchronize(a.st));
-        init_est = he[0];
-        thi = he[1];
+        thi = range_select(a, rs, alist, na, (const uint64_t *)sup, (const uint64_t *)wl, kmin, kmax, tgt, &init_est);
       }
     } else {
-      k_set_u64<<<1, 1, 0, a.st>>>(&rs->theta_hi, thi);
+      set_u64(a, (uint64_t *)&rs->theta_hi, thi);
     }
-    CK_LAUNCH();
     prev_init_est = init_est;
     cur_final = 0;
     // ---- snapshot + first active set (Alg. 4 l.6-9)
@@ -991,6 +930,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       R.o_len = o_len;
       R.part = part;
       R.pi = pi;
+      R.state = state;
       R.sum_w = sumw;
       R.lists = plists;
       R.counts = dc + 3;
