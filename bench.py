@@ -182,6 +182,84 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def timed(fn, dev, flush):
+    """Device time of fn() in ms with the L2 flushed first."""
+    import torch
+    flush.zero_()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def run_extra(args):
+    """Measurements of the other workloads (not the default bench line)."""
+    import torch
+    import bigraph_gen as gen
+    import paper_2110_12511_gb300 as pbng
+    from paper_2110_12511_gb300 import build as pbuild
+    pbuild.build()
+    pbng.lib()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    res = {"workload": args.workload}
+    if args.workload == "wing_chunglu_500k_100k_5m_planted":
+        t0 = time.time()
+        g = gen.make("chunglu_500k_100k_5m_planted")
+        res["gen_s"] = time.time() - t0
+        dg = pbng.to_device(g, dev)
+        P = 100
+        for _ in range(args.warmup):
+            pbng.wing_decompose(dg, P=P)
+        ms, st = [], None
+        for _ in range(args.steps):
+            t, (_, st) = timed(lambda: pbng.wing_decompose(dg, P=P, with_stats=True), dev, flush)
+            ms.append(t)
+        res.update({"m": g.m, "P": P, "ms": statistics.median(ms), "ms_all": ms,
+                    "updates_per_s": st["updates"] / (statistics.median(ms) / 1e3),
+                    "links_traversed_per_s": (st["wedges_cd"] + st["wedges_fd"]) / (statistics.median(ms) / 1e3),
+                    "stats": st})
+    elif args.workload == "tip_batch_4096":
+        t0 = time.time()
+        n = args.batch
+        gs = [gen.batch_graph(1000 + i) for i in range(n)]
+        res["gen_s"] = time.time() - t0
+        dgs = [pbng.to_device(g, dev) for g in gs]
+        res.update({"graphs": n, "edges": int(sum(g.m for g in gs))})
+        P = 150
+        pbng.tip_decompose_batch(dgs, "U", P=P)
+        tb, (_, stb) = timed(lambda: pbng.tip_decompose_batch(dgs, "U", P=P, with_stats=True), dev, flush)
+        def one_by_one():
+            w = 0
+            for d in dgs:
+                _, s1 = pbng.tip_decompose(d, "U", P=P, with_stats=True)
+                w += s1["wedges_count"] + s1["wedges_cd"] + s1["wedges_fd"]
+            return w
+        one_by_one_w = one_by_one() if n <= 64 else None
+        tp, wp = timed(one_by_one, dev, flush)
+        res.update({"P": P, "batched_ms": tb, "plain_one_by_one_ms": tp, "speedup": tp / tb,
+                    "batched_wedges_per_s": (stb["wedges_count"] + stb["wedges_cd"] + stb["wedges_fd"]) / (tb / 1e3),
+                    "batched_stats": stb, "plain_wedges": wp})
+    elif args.workload == "tip_chunglu_5m_1m_60m":
+        t0 = time.time()
+        g = gen.make("chunglu_5m_1m_60m")
+        res["gen_s"] = time.time() - t0
+        dg = pbng.to_device(g, dev)
+        P = 200
+        pbng.tip_decompose(dg, "U", P=P)
+        t, (_, st) = timed(lambda: pbng.tip_decompose(dg, "U", P=P, with_stats=True), dev, flush)
+        res.update({"m": g.m, "P": P, "ms": t, "wedges_per_s": (st["wedges_count"] + st["wedges_cd"] + st["wedges_fd"]) / (t / 1e3),
+                    "stats": st})
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -191,10 +269,13 @@ def main():
     ap.add_argument("--P", type=int, default=150)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--batch", type=int, default=4096)
     args = ap.parse_args()
     ws, rank, local = dist_info()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload != WORKLOAD:
+        return run_extra(args)
 
     import torch
     import torch.distributed as dist
@@ -212,7 +293,7 @@ def main():
         dist.barrier()
     pbng.lib()
 
-    g = gen.make(args.workload)
+    g = gen.make(WORKLOAD)
     dg = pbng.to_device(g, dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
@@ -316,7 +397,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic (seeded Chung-Lu generator)",
-            "config": {"workload": WORKLOAD_DESC, "name": args.workload, "P": args.P, "sides": "U,V",
+            "config": {"workload": WORKLOAD_DESC, "name": WORKLOAD, "P": args.P, "sides": "U,V",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write)", "nu": g.nu, "nv": g.nv, "m": g.m,
                        "wedges_per_step": wedges_step,
