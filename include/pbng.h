@@ -98,6 +98,11 @@ typedef struct pbng_stats {
   uint64_t ns_k_count, ns_k_peel, ns_k_fd;     /* counting / coarse peel / fine peel kernels */
   uint64_t bytes_count, bytes_peel, bytes_fd;  /* algorithmic bytes of those kernels */
   uint64_t n_k_count, n_k_peel, n_k_fd;        /* launches in each group */
+  uint64_t fd_work_max, fd_work_sum;           /* fine-phase work per partition (tip: wedges of
+                                                  G_i with both ends in U_i; wing: sum of init
+                                                  supports): largest and total, for imbalance */
+  uint64_t fd_part_steps_max;                  /* most fine-phase steps taken by one partition */
+  uint64_t fd_part_cycles_max;                 /* most SM clock cycles spent on one partition */
 } pbng_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -44,7 +44,7 @@ class Stats(ctypes.Structure):
         "wedge_bound", "ns_setup", "ns_count", "ns_cd", "ns_part", "ns_fd", "ns_total")] + [
         ("parts_used", ctypes.c_uint32), ("reserved", ctypes.c_uint32)] + [(n, ctypes.c_uint64) for n in (
         "launches", "ns_k_count", "ns_k_peel", "ns_k_fd", "bytes_count", "bytes_peel", "bytes_fd",
-        "n_k_count", "n_k_peel", "n_k_fd")]
+        "n_k_count", "n_k_peel", "n_k_fd", "fd_work_max", "fd_work_sum", "fd_part_steps_max", "fd_part_cycles_max")]
 
     def to_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "fdwin.cuh"
 #include "internal.cuh"
 #include "wedge.cuh"
 
@@ -510,10 +511,13 @@ struct FDArgs {
   uint8_t *state;
   ull *sup;  // starts as init
   ull *theta;
-  uint32_t *buf_a, *buf_b, *buf_f, *buf_big;  // per-partition regions (offset ps[p])
+  uint32_t *buf_a, *buf_b, *buf_c, *buf_d, *buf_f, *buf_big;  // per-partition regions (offset ps[p])
   uint32_t *gcnt;                             // per-partition dense counters (offset ps[p]), zeroed
   unsigned *queue;
   ull *wedges, *steps, *updates;
+  ull *pstat;  // per partition: steps, SM cycles
+  const uint32_t *seg_lo, *seg_len;  // per X-side edge: slice of (y, part(x)) in fd_adj
+  const uint32_t *w_fd;              // per vertex: wedges in its partition's subgraph
 };
 
 constexpr int FT = 512, FW = FT / 32;
@@ -538,9 +542,32 @@ __device__ __forceinline__ uint32_t fd_load(const FDArgs &A, uint32_t p, uint32_
                                             const Grp &g, FMid<N> &mb) {
   int r = g.rank();
   uint32_t lo = 0, len = 0;
-  if (base + r < xd) fd_seg(A, A.p_adj[xo + base + r], p, lo, len);
+  if (base + r < xd) {
+    lo = A.seg_lo[xo + base + r];
+    len = A.seg_len[xo + base + r];
+  }
   mb.lo[r] = lo;
   return g.scan(len, mb.pre);
+}
+
+// once per call: every X-side edge (x, y) gets the slice of y's partitioned
+// list that holds partition part(x), and every x its wedge count in G_part(x)
+__global__ void k_fd_segs(FDArgs A, uint32_t nx, const uint32_t *part, uint32_t *seg_lo, uint32_t *seg_len, uint32_t *w_fd) {
+  int lane = threadIdx.x & 31;
+  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t x = gw; x < nx; x += nw) {
+    uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo, p = part[x], W = 0;
+    for (uint32_t k = lane; k < xd; k += 32) {
+      uint32_t lo, len;
+      fd_seg(A, A.p_adj[xo + k], p, lo, len);
+      seg_lo[xo + k] = lo;
+      seg_len[xo + k] = len;
+      W += len;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
+    if (lane == 0) w_fd[x] = W;
+  }
 }
 
 template <class Grp, int N, class F>
@@ -555,8 +582,8 @@ __device__ __forceinline__ uint8_t ld_state(const uint8_t *s) { return *(volatil
 
 __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size_t dense_off) {
   extern __shared__ __align__(16) uint8_t sm[];
-  __shared__ uint32_t s_p, s_na, s_nf, s_nr, s_fidx, s_nbig;
-  __shared__ ull s_min, s_level;
+  __shared__ uint32_t s_p, s_fidx, s_nbig;
+  __shared__ FDShared S;
   __shared__ uint32_t ws[FT / 32 + 2];
   __shared__ ull ws64[FT / 32];
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -579,49 +606,30 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
     uint32_t p = s_p;
     if (p == 0xffffffffu) break;
     uint32_t base = A.ps[p], np = A.ps[p + 1] - base;
-    uint32_t *la = A.buf_a + base, *lb = A.buf_b + base, *lf = A.buf_f + base, *lbig = A.buf_big + base;
+    uint32_t *lf = A.buf_f + base, *lbig = A.buf_big + base;
+    FDLists L{{A.buf_a + base, A.buf_b + base}, {A.buf_c + base, A.buf_d + base}, lf};
     bool smem_dense = np <= P_DENSE;
     uint32_t *cnt = smem_dense ? dense : A.gcnt + base;
-    for (uint32_t j = threadIdx.x; j < np; j += FT) la[j] = A.xs[base + j];
+    for (uint32_t j = threadIdx.x; j < np; j += FT) L.a[0][j] = A.xs[base + j];
     if (threadIdx.x == 0) {
-      s_na = np;
-      s_level = 0;
+      S.na = np;
+      S.nc = 0;
+      S.pa = 0;
+      S.pc = 0;
+      S.level = 0;
     }
+    long long t_part = clock64();
+    ull p_steps = 0;
     __syncthreads();
-    while (s_na > 0) {
-      uint32_t na = s_na;
-      // running minimum of the remaining supports
-      if (threadIdx.x == 0) s_min = ~0ull;
-      __syncthreads();
-      ull mn = ~0ull;
-      for (uint32_t j = threadIdx.x; j < na; j += FT) mn = min(mn, __ldcg(&A.sup[la[j]]));
-#pragma unroll
-      for (int o = 16; o; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      if (lane == 0) atomicMin(&s_min, mn);
-      __syncthreads();
+    while (S.na + S.nc > 0) {
+      p_steps++;
+      // every vertex at the running minimum is peeled with tip number = level
+      uint32_t nf = fd_select<FT>(S, L, A.sup, A.theta, A.state, ST_PEELED, ST_PEELED);
       if (threadIdx.x == 0) {
-        s_level = max(s_level, s_min);
-        s_nf = 0;
-        s_nr = 0;
         s_fidx = 0;
         s_nbig = 0;
       }
       __syncthreads();
-      ull level = s_level;
-      // every vertex at the minimum is peeled with tip number = level
-      for (uint32_t j = threadIdx.x; j < na; j += FT) {
-        uint32_t x = la[j];
-        ull s = __ldcg(&A.sup[x]);
-        if (s <= level) {
-          lf[atomicAdd(&s_nf, 1u)] = x;
-          A.theta[x] = level;
-          A.state[x] = ST_PEELED;
-        } else {
-          lb[atomicAdd(&s_nr, 1u)] = x;
-        }
-      }
-      __syncthreads();
-      uint32_t nf = s_nf;
       my_steps++;
       // warp-per-vertex updates for vertices with few wedges in G_p
       for (;;) {
@@ -631,14 +639,7 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
         if (k >= nf) break;
         uint32_t x = lf[k];
         uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
-        uint32_t W = 0;
-        for (uint32_t b0 = 0; b0 < xd; b0 += 32) {
-          uint32_t lo = 0, len = 0;
-          if (b0 + lane < xd) fd_seg(A, A.p_adj[xo + b0 + lane], p, lo, len);
-#pragma unroll
-          for (int o = 16; o; o >>= 1) len += __shfl_xor_sync(0xffffffffu, len, o);
-          W += len;
-        }
+        uint32_t W = A.w_fd[x];
         if (W < 2) continue;
         if (W > PW_MAXW) {
           if (lane == 0) lbig[atomicAdd(&s_nbig, 1u)] = x;
@@ -659,7 +660,8 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
           if (kk != EMPTY_KEY) {
             uint32_t c = wval[i];
             if (c >= 2) {
-              atomicAdd(&A.sup[kk], (ull)(0ull - choose2(c)));
+              ull dec = choose2(c);
+              fd_crossing(S, L, kk, atomicAdd(&A.sup[kk], (ull)(0ull - dec)), dec);
               my_updates++;
             }
             wkey[i] = EMPTY_KEY;
@@ -688,18 +690,19 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
             if (ld_state(&A.state[xp]) != ST_ALIVE) return;
             uint32_t c = atomicExch(&cnt[A.loc[xp]], 0u);
             if (c >= 2) {
-              atomicAdd(&A.sup[xp], (ull)(0ull - choose2(c)));
+              ull dec = choose2(c);
+              fd_crossing(S, L, xp, atomicAdd(&A.sup[xp], (ull)(0ull - dec)), dec);
               my_updates++;
             }
           });
           __syncthreads();
         }
       }
-      if (threadIdx.x == 0) s_na = s_nr;
-      uint32_t *t = la;
-      la = lb;
-      lb = t;
       __syncthreads();
+    }
+    if (threadIdx.x == 0 && A.pstat) {
+      A.pstat[2 * p] = p_steps;
+      A.pstat[2 * p + 1] = (ull)(clock64() - t_part);
     }
   }
   my_wedges = bg.sum64(my_wedges);
@@ -1057,6 +1060,8 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   F.theta = (ull *)theta_out;
   F.buf_a = alist;
   F.buf_b = alist2;
+  F.buf_c = a.alloc<uint32_t>(nx);
+  F.buf_d = a.alloc<uint32_t>(nx);
   F.buf_f = front;
   F.buf_big = front2;
   F.gcnt = a.zeros<uint32_t>(nx);
@@ -1065,6 +1070,14 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   F.wedges = dwedge + 6;
   F.steps = dwedge + 7;
   F.updates = dwedge + 9;
+  ull *pstat = a.zeros<ull>(2 * (size_t)nparts);
+  F.pstat = pstat;
+  uint32_t *seg_lo = a.alloc<uint32_t>(G.m), *seg_len = a.alloc<uint32_t>(G.m), *w_fd = a.alloc<uint32_t>(nx);
+  k_fd_segs<<<grid_for((size_t)nx * 32, T, cap), T, 0, a.st>>>(F, nx, part, seg_lo, seg_len, w_fd);
+  CK_LAUNCH();
+  F.seg_lo = seg_lo;
+  F.seg_len = seg_len;
+  F.w_fd = w_fd;
   unsigned fgrid = std::min<unsigned>(nparts, sms);
   g_prof.begin(PROF_FD);
   k_fd_tip<<<fgrid, FT, fd_smem(), a.st>>>(F, fd_warp_bytes(), fd_dense_off());
@@ -1097,6 +1110,16 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     st->ns_part += (uint64_t)(t23 * 1e6);
     st->ns_fd += (uint64_t)(t34 * 1e6);
     st->parts_used = nparts;
+    for (uint32_t i = 0; i < nparts; i++) {
+      st->fd_work_sum += hwork[i];
+      if (hwork[i] > st->fd_work_max) st->fd_work_max = hwork[i];
+    }
+    std::vector<ull> ps_h(2 * (size_t)nparts);
+    CK(cudaMemcpy(ps_h.data(), pstat, ps_h.size() * 8, cudaMemcpyDeviceToHost));
+    for (uint32_t i = 0; i < nparts; i++) {
+      st->fd_part_steps_max = std::max<uint64_t>(st->fd_part_steps_max, ps_h[2 * i]);
+      st->fd_part_cycles_max = std::max<uint64_t>(st->fd_part_cycles_max, ps_h[2 * i + 1]);
+    }
   }
   for (auto &e : ev) cudaEventDestroy(e);
 }

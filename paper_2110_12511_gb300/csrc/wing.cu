@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "fdwin.cuh"
 #include "internal.cuh"
 #include "wedge.cuh"
 
@@ -464,23 +465,71 @@ __global__ void k_fd_reset(uint8_t *palive, size_t np, uint8_t *state, uint32_t 
   }
 }
 
+// links (e, B) kept in the index of e's own partition: pmin(q) == part(e)
+__global__ void k_flink_count(const uint32_t *eoff, const uint32_t *elink, const uint32_t *pmin, const uint32_t *part,
+                              uint32_t m, uint32_t *fdeg) {
+  int lane = threadIdx.x & 31;
+  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t e = gw; e < m; e += nw) {
+    uint32_t p = part[e], c = 0;
+    for (uint32_t k = eoff[e] + lane; k < eoff[e + 1]; k += 32) c += pmin[elink[k]] == p;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) fdeg[e] = c;
+  }
+}
+
+__global__ void k_flink_fill(const uint32_t *eoff, const uint32_t *elink, const uint32_t *pmin, const uint32_t *part,
+                             uint32_t m, const uint32_t *foff, uint32_t *flink) {
+  int lane = threadIdx.x & 31;
+  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t e = gw; e < m; e += nw) {
+    uint32_t p = part[e], out = foff[e];
+    for (uint32_t k = eoff[e]; k < eoff[e + 1]; k += 32) {
+      uint32_t q = 0;
+      bool keep = false;
+      if (k + lane < eoff[e + 1]) {
+        q = elink[k + lane];
+        keep = pmin[q] == p;
+      }
+      unsigned b = __ballot_sync(0xffffffffu, keep);
+      if (keep) flink[out + __popc(b & ((1u << lane) - 1u))] = q;
+      out += __popc(b);
+    }
+  }
+}
+
+__global__ void k_group_len(const uint32_t *gstart, uint32_t ng, uint32_t *glen) {
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < ng; g += (size_t)gridDim.x * blockDim.x)
+    glen[g] = gstart[g + 1] - gstart[g];
+}
+
 struct WFDArgs {
   const uint32_t *pe1, *pe2, *eoff, *elink, *pmin, *pb_of, *order, *gstart, *gps;
   const uint32_t *part, *es, *ps, *orderp;  // edges grouped by partition, partition offsets, LPT order
   uint32_t *gk, *gcnt;
   uint8_t *palive, *state;
   ull *sup, *theta;
-  uint32_t *buf_a, *buf_b, *buf_f, *gtouch;  // per-partition regions
+  uint32_t *buf_a, *buf_b, *buf_c, *buf_d, *buf_f, *gtouch;  // per-partition regions
   uint32_t nparts;
   unsigned *queue;
   ull *ctr;  // [0] links, [1] updates, [2] steps
+  ull *pstat;  // per partition: steps, SM cycles
+  const uint32_t *foff, *flink;  // per edge: its links in its own partition's index
+  uint32_t *glen;                // live prefix of each group's pair list in order
+  uint32_t *gdead;               // pairs removed since the group's last compaction
+  uint32_t *order_w;             // writable alias of order (compaction)
 };
 
 constexpr int WFT = 512;
 
 __global__ void __launch_bounds__(WFT) k_wing_fd(WFDArgs A) {
-  __shared__ uint32_t s_p, s_na, s_nf, s_nr, s_nt;
-  __shared__ ull s_min, s_level;
+  __shared__ uint32_t s_p, s_nt, s_nc;
+  __shared__ FDShared S;
+  __shared__ uint32_t s_itm[WFT], s_lo[WFT], s_pre[WFT + 1];
+  __shared__ uint32_t ws[WFT / 32 + 2];
+  __shared__ ull ws64[WFT / 32];
+  BlockGrp<WFT> bg{ws, ws64};
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   ull links = 0, ups = 0, steps = 0;
   for (;;) {
@@ -492,49 +541,40 @@ __global__ void __launch_bounds__(WFT) k_wing_fd(WFDArgs A) {
     uint32_t p = s_p;
     if (p == 0xffffffffu) break;
     uint32_t base = A.ps[p], np = A.ps[p + 1] - base;
-    uint32_t *la = A.buf_a + base, *lb = A.buf_b + base, *lf = A.buf_f + base, *gt = A.gtouch + A.gps[p];
-    for (uint32_t j = threadIdx.x; j < np; j += WFT) la[j] = A.es[base + j];
+    uint32_t *lf = A.buf_f + base, *gt = A.gtouch + 2 * A.gps[p];
+    FDLists L{{A.buf_a + base, A.buf_b + base}, {A.buf_c + base, A.buf_d + base}, lf};
+    for (uint32_t j = threadIdx.x; j < np; j += WFT) L.a[0][j] = A.es[base + j];
     if (threadIdx.x == 0) {
-      s_na = np;
-      s_level = 0;
+      S.na = np;
+      S.nc = 0;
+      S.pa = 0;
+      S.pc = 0;
+      S.level = 0;
     }
+    long long t_part = clock64();
+    ull p_steps = 0;
     __syncthreads();
-    while (s_na > 0) {
-      uint32_t na = s_na;
-      if (threadIdx.x == 0) s_min = ~0ull;
+    while (S.na + S.nc > 0) {
+      p_steps++;
+      uint32_t nf = fd_select<WFT>(S, L, A.sup, A.theta, A.state, ST_ACTIVE, ST_PEELED);
+      if (threadIdx.x == 0) s_nt = 0;
       __syncthreads();
-      ull mn = ~0ull;
-      for (uint32_t j = threadIdx.x; j < na; j += WFT) mn = min(mn, __ldcg(&A.sup[la[j]]));
-      for (int o = 16; o; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      if (lane == 0) atomicMin(&s_min, mn);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        s_level = max(s_level, s_min);
-        s_nf = 0;
-        s_nr = 0;
-        s_nt = 0;
-      }
-      __syncthreads();
-      ull level = s_level;
-      for (uint32_t j = threadIdx.x; j < na; j += WFT) {
-        uint32_t e = la[j];
-        if (__ldcg(&A.sup[e]) <= level) {
-          lf[atomicAdd(&s_nf, 1u)] = e;
-          A.theta[e] = level;
-          A.state[e] = ST_ACTIVE;
-        } else {
-          lb[atomicAdd(&s_nr, 1u)] = e;
-        }
-      }
-      __syncthreads();
-      uint32_t nf = s_nf;
       steps++;
-      // pass 1 restricted to I_p: warp per peeled edge
-      for (uint32_t j = warp; j < nf; j += WFT / 32) {
-        uint32_t e = lf[j];
-        for (uint32_t k = A.eoff[e] + lane; k < A.eoff[e + 1]; k += 32) {
-          uint32_t q = A.elink[k];
-          if (A.pmin[q] != p) continue;  // link not in I_p
+      // pass 1 restricted to I_p, flattened over (peeled edge, link) so the
+      // whole block shares a few long link lists
+      for (uint32_t c0 = 0; c0 < nf; c0 += WFT) {
+        uint32_t r = threadIdx.x, lo = 0, len = 0;
+        if (c0 + r < nf) {
+          uint32_t e = lf[c0 + r];
+          s_itm[r] = e;
+          lo = A.foff[e];
+          len = A.foff[e + 1] - lo;
+        }
+        s_lo[r] = lo;
+        uint32_t T = bg.scan(len, s_pre);
+        for (uint32_t w = r; w < T; w += WFT) {
+          int i = seg_of(s_pre, WFT, w);
+          uint32_t e = s_itm[i], q = A.flink[s_lo[i] + (w - s_pre[i])];  // a link of e in I_p
           links++;
           if (!*(volatile uint8_t *)&A.palive[q]) continue;
           uint32_t a = A.pe1[q], b = A.pe2[q];
@@ -546,38 +586,81 @@ __global__ void __launch_bounds__(WFT) k_wing_fd(WFDArgs A) {
           A.palive[q] = 0;
           if (in_p && st == ST_ALIVE) {
             uint32_t kb = A.gk[g];
-            if (kb >= 2) atomicAdd(&A.sup[et], (ull)(0ull - (ull)(kb - 1))), ups++;
+            if (kb >= 2) {
+              ull old = atomicAdd(&A.sup[et], (ull)(0ull - (ull)(kb - 1)));
+              fd_crossing(S, L, et, old, kb - 1);
+              ups++;
+            }
           }
           if (atomicAdd(&A.gcnt[g], 1u) == 0u) gt[atomicAdd(&s_nt, 1u)] = g;
         }
+        __syncthreads();
       }
-      __syncthreads();
-      // pass 2 restricted to I_p: warp per touched group (B, p)
+      // pass 2 restricted to I_p, flattened over (touched group, live pair)
       uint32_t nt = s_nt;
-      for (uint32_t j = warp; j < nt; j += WFT / 32) {
-        uint32_t g = gt[j];
-        uint32_t c = A.gcnt[g];
-        for (uint32_t k = A.gstart[g] + lane; k < A.gstart[g + 1]; k += 32) {
-          uint32_t q = A.order[k];
+      for (uint32_t c0 = 0; c0 < nt; c0 += WFT) {
+        uint32_t r = threadIdx.x, lo = 0, len = 0;
+        if (c0 + r < nt) {
+          uint32_t g = gt[c0 + r];
+          s_itm[r] = g;
+          lo = A.gstart[g];
+          len = A.glen[g];
+        }
+        s_lo[r] = lo;
+        uint32_t T = bg.scan(len, s_pre);
+        for (uint32_t w = r; w < T; w += WFT) {
+          int i = seg_of(s_pre, WFT, w);
+          uint32_t g = s_itm[i], q = A.order_w[s_lo[i] + (w - s_pre[i])];
           links++;
           if (!A.palive[q]) continue;
+          uint32_t c = A.gcnt[g];
           uint32_t a = A.pe1[q], b = A.pe2[q];
-          if (A.part[a] == p && A.state[a] == ST_ALIVE) atomicAdd(&A.sup[a], (ull)(0ull - c)), ups++;
-          if (A.part[b] == p && A.state[b] == ST_ALIVE) atomicAdd(&A.sup[b], (ull)(0ull - c)), ups++;
+          if (A.part[a] == p && A.state[a] == ST_ALIVE) fd_crossing(S, L, a, atomicAdd(&A.sup[a], (ull)(0ull - c)), c), ups++;
+          if (A.part[b] == p && A.state[b] == ST_ALIVE) fd_crossing(S, L, b, atomicAdd(&A.sup[b], (ull)(0ull - c)), c), ups++;
         }
-        __syncwarp();
+        __syncthreads();
+      }
+      // bloom numbers, and lazy compaction of groups a quarter dead
+      if (threadIdx.x == 0) s_nc = 0;
+      __syncthreads();
+      for (uint32_t j = threadIdx.x; j < nt; j += WFT) {
+        uint32_t g = gt[j], c = A.gcnt[g];
+        A.gk[g] -= c;
+        A.gcnt[g] = 0;
+        uint32_t d = A.gdead[g] + c;
+        A.gdead[g] = d;
+        if (4 * d >= A.glen[g]) gt[nt + atomicAdd(&s_nc, 1u)] = g;  // queued after the touched list
+      }
+      __syncthreads();
+      uint32_t nc = s_nc;
+      for (uint32_t j = warp; j < nc; j += WFT / 32) {
+        uint32_t g = gt[nt + j];
+        uint32_t lo = A.gstart[g], len = A.glen[g], out = 0;
+        for (uint32_t k = 0; k < len; k += 32) {
+          uint32_t q = 0;
+          bool live = false;
+          if (k + lane < len) {
+            q = A.order_w[lo + k + lane];
+            live = A.palive[q];
+          }
+          unsigned bal = __ballot_sync(0xffffffffu, live);
+          __syncwarp();
+          if (live) A.order_w[lo + out + __popc(bal & ((1u << lane) - 1u))] = q;
+          out += __popc(bal);
+          __syncwarp();
+        }
         if (lane == 0) {
-          A.gk[g] -= c;
-          A.gcnt[g] = 0;
+          A.glen[g] = out;
+          A.gdead[g] = 0;
         }
       }
       __syncthreads();
       for (uint32_t j = threadIdx.x; j < nf; j += WFT) A.state[lf[j]] = ST_PEELED;
-      if (threadIdx.x == 0) s_na = s_nr;
-      uint32_t *t = la;
-      la = lb;
-      lb = t;
       __syncthreads();
+    }
+    if (threadIdx.x == 0 && A.pstat) {
+      A.pstat[2 * p] = p_steps;
+      A.pstat[2 * p + 1] = (ull)(clock64() - t_part);
     }
   }
   for (int o = 16; o; o >>= 1) links += __shfl_xor_sync(0xffffffffu, links, o), ups += __shfl_xor_sync(0xffffffffu, ups, o);
@@ -881,7 +964,7 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   CK(cudaMemcpyAsync(sup, init, (size_t)m * 8, cudaMemcpyDeviceToDevice, a.st));
   k_fd_reset<<<grid_for(std::max(np, (size_t)m), T, cap), T, 0, a.st>>>(palive, np, state, m);
   CK_LAUNCH();
-  uint32_t *gcnt = a.zeros<uint32_t>((size_t)ngroups + 1), *gtouch = a.alloc<uint32_t>((size_t)ngroups + 1);
+  uint32_t *gcnt = a.zeros<uint32_t>((size_t)ngroups + 1), *gtouch = a.alloc<uint32_t>(2 * (size_t)ngroups + 2);
   WFDArgs W;
   W.pe1 = pe1;
   W.pe2 = pe2;
@@ -904,12 +987,37 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   W.theta = (ull *)theta_out;
   W.buf_a = alist;
   W.buf_b = alist2;
+  W.buf_c = a.alloc<uint32_t>(m);
+  W.buf_d = a.alloc<uint32_t>(m);
   W.buf_f = front;
   W.gtouch = gtouch;
   W.nparts = nparts;
   W.queue = dc + 8;
   CK(cudaMemsetAsync(dc + 8, 0, 4, a.st));
   W.ctr = wctr + 4;
+  ull *pstat = a.zeros<ull>(2 * (size_t)nparts);
+  W.pstat = pstat;
+  {
+    uint32_t *fdeg = a.zeros<uint32_t>((size_t)m + 1), *foff = a.alloc<uint32_t>((size_t)m + 1);
+    k_flink_count<<<grid_for((size_t)m * 32, T, cap), T, 0, a.st>>>(eoff, elink, pmin, part, m, fdeg);
+    CK_LAUNCH();
+    exclusive_scan_u32(a, fdeg, foff, m);
+    uint32_t nfl = fetch(a, foff + m);
+    uint32_t *flink = a.alloc<uint32_t>((size_t)nfl + 1);
+    k_flink_fill<<<grid_for((size_t)m * 32, T, cap), T, 0, a.st>>>(eoff, elink, pmin, part, m, foff, flink);
+    CK_LAUNCH();
+    a.free(fdeg);
+    W.foff = foff;
+    W.flink = flink;
+    uint32_t *glen = a.alloc<uint32_t>((size_t)ngroups + 1);
+    if (ngroups) {
+      k_group_len<<<grid_for(ngroups, T, cap), T, 0, a.st>>>(gstart, ngroups, glen);
+      CK_LAUNCH();
+    }
+    W.glen = glen;
+    W.gdead = a.zeros<uint32_t>((size_t)ngroups + 1);
+    W.order_w = order;
+  }
   g_prof.begin(PROF_FD);
   k_wing_fd<<<std::min<unsigned>(nparts, 2 * sms), WFT, 0, a.st>>>(W);
   CK_LAUNCH();
@@ -940,6 +1048,16 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
     st->ns_part += (uint64_t)(t23 * 1e6);
     st->ns_fd += (uint64_t)(t34 * 1e6);
     st->parts_used = nparts;
+    for (uint32_t i = 0; i < nparts; i++) {
+      st->fd_work_sum += hwork[i];
+      if (hwork[i] > st->fd_work_max) st->fd_work_max = hwork[i];
+    }
+    std::vector<ull> ps_h(2 * (size_t)nparts);
+    CK(cudaMemcpy(ps_h.data(), pstat, ps_h.size() * 8, cudaMemcpyDeviceToHost));
+    for (uint32_t i = 0; i < nparts; i++) {
+      st->fd_part_steps_max = std::max<uint64_t>(st->fd_part_steps_max, ps_h[2 * i]);
+      st->fd_part_cycles_max = std::max<uint64_t>(st->fd_part_cycles_max, ps_h[2 * i + 1]);
+    }
     st->bytes_count += 4 * hcc[0] + 12 * hcc[1] + 16 * hcc[2];
     st->bytes_peel += 8 * hw[0] + 16 * hw[1] + 8 * front_total;
     st->bytes_fd += 8 * hw[4] + 16 * hw[5] + 8 * (uint64_t)m;
