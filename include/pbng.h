@@ -56,7 +56,8 @@ typedef enum { PBNG_SIDE_U = 0, PBNG_SIDE_V = 1 } pbng_side;
 
 enum {
   PBNG_BOUNDS_ESTIMATOR = 0, /* find_range with adaptive targets (Sec. 3.1.3) */
-  PBNG_BOUNDS_EXPLICIT = 2   /* caller-supplied bounds (e.g. from a learned proposer) */
+  PBNG_BOUNDS_LEARNED = 1,   /* bounds proposed by the MLP in opts->mlp_params (pbng_mlp_forward) */
+  PBNG_BOUNDS_EXPLICIT = 2   /* caller-supplied bounds */
 };
 enum { PBNG_MEM_DEVICE = 0, PBNG_MEM_HOST = 1 };
 
@@ -73,6 +74,13 @@ typedef struct pbng_opts {
                               device-side loop (no host round trip per round); default 0 */
   uint64_t timeout_ns;     /* limit for bounded device waits; 0 = 10 s */
   void *stream;            /* cudaStream_t */
+  const float *mlp_params; /* LEARNED (tip): device float32 parameters, layout of pbng_mlp_forward,
+                              in = 128 features of pbng_bound_features, out = bounds proposed */
+  uint32_t mlp_hidden, mlp_out;
+  uint64_t *bounds_out;    /* optional host array receiving the upper bounds theta(2), theta(3), ...
+                              actually used (the last, unbounded range is not listed) */
+  uint32_t n_bounds_out;   /* capacity of bounds_out; the count written is stats->parts_used - 1
+                              (at most this many are stored) */
 } pbng_opts;
 
 typedef struct pbng_stats {
@@ -168,6 +176,31 @@ int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng_side side,
 int pbng_vertex_counts_noalloc(uint32_t nu, uint32_t nv, uint64_t m, const uint64_t *u_off,
                                const uint32_t *u_adj, const uint64_t *v_off, const uint32_t *v_adj,
                                uint64_t *out_u, void *stream);
+
+/* Features of the learned bound proposer (no counterpart in the paper's
+ * method; the bounds it feeds only change speed, Sec. 4.1 Th. 2): out[0..63]
+ * = fractions of the peeled side's vertices per half-octave degree bin
+ * (bin 0: d = 0, 1: d = 1, else 2L-2 + the second-highest bit of d, L = bit
+ * length), out[64..127] = fractions of vertices whose initial butterfly count
+ * (Sec. 2.1) has a bit length j bits below that of the largest count (j = 0..63).
+ * The proposer's outputs are relative to the largest count K:
+ * y_i = log2(1 + b_i) / log2(1 + K).  out: 128 floats of device memory. */
+int pbng_bound_features(const pbng_bigraph *g, pbng_side side, float *out, const pbng_opts *opts);
+
+/* MLP of the learned proposer, FP32, on the device.  params packs
+ * [W1 (in x hidden), b1, W2 (hidden x hidden), b2, W3 (hidden x out), b3]
+ * row-major; y = relu(relu(x W1 + b1) W2 + b2) W3 + b3 for each of the B
+ * rows of X (B x in) into Y (B x out).  All pointers are device pointers;
+ * each call synchronises `stream`. */
+int pbng_mlp_forward(const float *params, uint32_t in, uint32_t hidden, uint32_t out, const float *X, uint32_t B,
+                     float *Y, void *stream);
+/* Gradient of the mean squared error (1/(B out)) sum (y - t)^2 with respect
+ * to params (same layout) into grad, and the loss into *loss (device). */
+int pbng_mlp_grad(const float *params, uint32_t in, uint32_t hidden, uint32_t out, const float *X, const float *T,
+                  uint32_t B, float *grad, float *loss, void *stream);
+/* One Adam step (bias-corrected, step >= 1) over n parameters. */
+int pbng_mlp_adam(float *params, const float *grad, float *m, float *v, uint64_t n, float lr, float beta1, float beta2,
+                  float eps, uint32_t step, void *stream);
 
 /* Name of a status code. */
 const char *pbng_strerror(int status);

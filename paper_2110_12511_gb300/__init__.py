@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libpbng.so")
 
 PBNG_OK, PBNG_EINVAL, PBNG_ENOMEM, PBNG_ECUDA, PBNG_ETIMEOUT, PBNG_EOVERFLOW, PBNG_EBOUNDS = 0, -1, -2, -3, -4, -5, -6
 SIDE_U, SIDE_V = 0, 1
-BOUNDS_ESTIMATOR, BOUNDS_EXPLICIT = 0, 2
+BOUNDS_ESTIMATOR, BOUNDS_LEARNED, BOUNDS_EXPLICIT = 0, 1, 2
 MEM_DEVICE, MEM_HOST = 0, 1
 
 
@@ -35,7 +35,9 @@ class Bigraph(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("bounds_mode", ctypes.c_int), ("bounds", ctypes.c_void_p), ("n_bounds", ctypes.c_uint32),
                 ("recount", ctypes.c_int), ("compact", ctypes.c_int), ("mem", ctypes.c_int),
-                ("graph_rounds", ctypes.c_int), ("timeout_ns", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+                ("graph_rounds", ctypes.c_int), ("timeout_ns", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+                ("mlp_params", ctypes.c_void_p), ("mlp_hidden", ctypes.c_uint32), ("mlp_out", ctypes.c_uint32),
+                ("bounds_out", ctypes.c_void_p), ("n_bounds_out", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -92,6 +94,15 @@ def lib():
         L.pbng_last_error_detail.restype = ctypes.c_char_p
         L.pbng_version.argtypes = []
         L.pbng_version.restype = C
+        L.pbng_bound_features.argtypes = [G, C, P, O]
+        L.pbng_bound_features.restype = C
+        L.pbng_mlp_forward.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_uint32, P, P]
+        L.pbng_mlp_forward.restype = C
+        L.pbng_mlp_grad.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, P, ctypes.c_uint32, P, P, P]
+        L.pbng_mlp_grad.restype = C
+        L.pbng_mlp_adam.argtypes = [P, P, P, P, ctypes.c_uint64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_uint32, P]
+        L.pbng_mlp_adam.restype = C
         L.pbng_vertex_counts_noalloc.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, P, P, P, P, P, P]
         L.pbng_vertex_counts_noalloc.restype = C
         _lib = L
@@ -133,7 +144,8 @@ def to_device(g, device="cuda") -> DeviceGraph:
     return DeviceGraph(int(g.nu), int(g.nv), off, adj)
 
 
-def _opts(stream=None, bounds=None, recount=True, compact=True, mem=MEM_DEVICE, graph_rounds=False, keep=None):
+def _opts(stream=None, bounds=None, recount=True, compact=True, mem=MEM_DEVICE, graph_rounds=False, keep=None,
+          mlp=None, bounds_out=None):
     o = Opts()
     lib().pbng_opts_init(ctypes.byref(o))
     o.recount = int(bool(recount))
@@ -155,6 +167,13 @@ def _opts(stream=None, bounds=None, recount=True, compact=True, mem=MEM_DEVICE, 
         o.bounds_mode = BOUNDS_EXPLICIT
         o.bounds = b.ctypes.data_as(ctypes.c_void_p)
         o.n_bounds = b.size
+    if mlp is not None:  # (params tensor on the device, hidden, out)
+        o.bounds_mode = BOUNDS_LEARNED
+        o.mlp_params = ctypes.c_void_p(mlp[0].data_ptr())
+        o.mlp_hidden, o.mlp_out = int(mlp[1]), int(mlp[2])
+    if bounds_out is not None:
+        o.bounds_out = bounds_out.ctypes.data_as(ctypes.c_void_p)
+        o.n_bounds_out = bounds_out.size
     return o
 
 
@@ -186,19 +205,65 @@ def _side(side) -> int:
 
 
 def tip_decompose(dg: DeviceGraph, side="U", P=150, bounds=None, recount=True, compact=True, graph_rounds=False,
-                  stream=None, with_stats=False):
-    """Tip numbers of one side (two-phase PBNG, Sec. 3.1-3.2)."""
+                  stream=None, with_stats=False, mlp=None, bounds_out=None):
+    """Tip numbers of one side (two-phase PBNG, Sec. 3.1-3.2).
+
+    bounds: explicit upper bounds; mlp: (params, hidden, out) of the learned
+    proposer; bounds_out: numpy uint64 array receiving the bounds used."""
     import torch
     s = _side(side)
     n = dg.nu if s == SIDE_U else dg.nv
     out = torch.empty(max(n, 1), dtype=torch.int64, device=dg.u_off.device)
     keep = []
-    o = _opts(stream, bounds, recount, compact, graph_rounds=graph_rounds, keep=keep)
+    o = _opts(stream, bounds, recount, compact, graph_rounds=graph_rounds, keep=keep, mlp=mlp, bounds_out=bounds_out)
     st = Stats()
     g = dg.c_struct()
     rc = lib().pbng_tip_decompose(ctypes.byref(g), s, int(P), out.data_ptr(), ctypes.byref(o), ctypes.byref(st))
     _check(rc, "pbng_tip_decompose")
     return (out[:n], st.to_dict()) if with_stats else out[:n]
+
+
+def bound_features(dg: DeviceGraph, side="U", stream=None):
+    """128 histogram features of the learned bound proposer (float32 tensor)."""
+    import torch
+    out = torch.zeros(128, dtype=torch.float32, device=dg.u_off.device)
+    o = _opts(stream)
+    g = dg.c_struct()
+    _check(lib().pbng_bound_features(ctypes.byref(g), _side(side), out.data_ptr(), ctypes.byref(o)),
+           "pbng_bound_features")
+    return out
+
+
+def _cs(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def mlp_forward(params, dims, X, stream=None):
+    """y = MLP(x) for the rows of X (device float32); dims = (in, hidden, out)."""
+    import torch
+    nin, hid, out = dims
+    Y = torch.empty((X.shape[0], out), dtype=torch.float32, device=X.device)
+    _check(lib().pbng_mlp_forward(params.data_ptr(), nin, hid, out, X.data_ptr(), X.shape[0], Y.data_ptr(), _cs(stream)),
+           "pbng_mlp_forward")
+    return Y
+
+
+def mlp_grad(params, dims, X, T, stream=None):
+    """(gradient of the mean squared error w.r.t. params, loss)."""
+    import torch
+    nin, hid, out = dims
+    grad = torch.empty_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+    _check(lib().pbng_mlp_grad(params.data_ptr(), nin, hid, out, X.data_ptr(), T.data_ptr(), X.shape[0],
+                               grad.data_ptr(), loss.data_ptr(), _cs(stream)), "pbng_mlp_grad")
+    return grad, float(loss.item())
+
+
+def mlp_adam(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().pbng_mlp_adam(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), params.numel(),
+                               lr, beta1, beta2, eps, step, _cs(stream)), "pbng_mlp_adam")
 
 
 def tip_decompose_host(g, side="U", P=150, with_stats=False, **kw):

@@ -88,8 +88,11 @@ __global__ void k_gather_lab(const unsigned long long *cnt_lab, const uint32_t *
 
 TipParams tip_params(uint32_t P, const pbng_opts &o) {
   if (P == 0) fail(PBNG_EINVAL, "P must be >= 1");
-  if (o.bounds_mode != PBNG_BOUNDS_ESTIMATOR && o.bounds_mode != PBNG_BOUNDS_EXPLICIT)
+  if (o.bounds_mode != PBNG_BOUNDS_ESTIMATOR && o.bounds_mode != PBNG_BOUNDS_EXPLICIT &&
+      o.bounds_mode != PBNG_BOUNDS_LEARNED)
     fail(PBNG_EINVAL, "unknown bounds_mode %d", o.bounds_mode);
+  if (o.bounds_mode == PBNG_BOUNDS_LEARNED && (!o.mlp_params || !o.mlp_hidden || !o.mlp_out))
+    fail(PBNG_EINVAL, "learned bounds need mlp_params, mlp_hidden and mlp_out");
   if (o.bounds_mode == PBNG_BOUNDS_EXPLICIT) {
     if (o.n_bounds && !o.bounds) fail(PBNG_EINVAL, "null bounds with n_bounds > 0");
     for (uint32_t i = 1; i < o.n_bounds; i++)
@@ -104,6 +107,10 @@ TipParams tip_params(uint32_t P, const pbng_opts &o) {
   p.compact = o.compact;
   p.graph_rounds = o.graph_rounds;
   p.timeout_ns = o.timeout_ns ? o.timeout_ns : 10000000000ull;
+  p.mlp_params = o.mlp_params;
+  p.mlp_hidden = o.mlp_hidden;
+  p.mlp_out = o.mlp_out;
+  p.bounds_used = nullptr;
   return p;
 }
 
@@ -260,9 +267,13 @@ int pbng_tip_decompose(const pbng_bigraph *g, pbng_side side, uint32_t P, uint64
       CK(cudaStreamSynchronize(a.st));
       t_setup = tm.ns();
     }
+    std::vector<uint64_t> used;
+    p.bounds_used = &used;
     tip_decompose(a, G, side == PBNG_SIDE_U ? 0 : 1, p, out.dev, stats ? &st : nullptr);
     out.finish(a);
     CK(cudaStreamSynchronize(a.st));
+    if (o.bounds_out)
+      for (size_t i = 0; i < used.size() && i < o.n_bounds_out; i++) o.bounds_out[i] = used[i];
     if (stats) {
       *stats = st;
       stats->ns_setup = t_setup;
@@ -291,15 +302,45 @@ int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, c
     memset(&st, 0, sizeof(st));
     CK(cudaStreamSynchronize(a.st));
     uint64_t t_setup = tm.ns();
+    std::vector<uint64_t> used;
+    p.bounds_used = &used;
     wing_decompose(a, G, p, out.dev, stats ? &st : nullptr);
     out.finish(a);
     CK(cudaStreamSynchronize(a.st));
+    if (o.bounds_out)
+      for (size_t i = 0; i < used.size() && i < o.n_bounds_out; i++) o.bounds_out[i] = used[i];
     if (stats) {
       *stats = st;
       stats->ns_setup = t_setup;
       stats->ns_total = tm.ns();
       ps.fill();
     }
+  });
+}
+
+int pbng_bound_features(const pbng_bigraph *g, pbng_side side, float *out, const pbng_opts *opts) {
+  pbng_opts o = opts ? *opts : defaults();
+  return guarded([&] {
+    if (side != PBNG_SIDE_U && side != PBNG_SIDE_V) fail(PBNG_EINVAL, "side must be PBNG_SIDE_U or PBNG_SIDE_V");
+    if (!out) fail(PBNG_EINVAL, "null output");
+    check_graph(g);
+    init_device_pool();
+    Arena a((cudaStream_t)o.stream);
+    pbng_bigraph d = device_graph(a, g, o.mem);
+    Graph G;
+    build_graph(a, d, true, false, G);
+    uint32_t nx = side == PBNG_SIDE_U ? G.nu : G.nv;
+    uint64_t *cnt = a.zeros<uint64_t>((size_t)G.n + 1), *sup = a.alloc<uint64_t>((size_t)nx + 1);
+    CountOut co;
+    co.cnt_lab = cnt;
+    count_butterflies(a, G, co);
+    if (nx) {
+      k_gather_lab<<<grid_for(nx, 256, 16 * num_sms()), 256, 0, a.st>>>((unsigned long long *)cnt, G.g2lab,
+                                                                          side == PBNG_SIDE_U ? 0 : G.nu, nx, sup);
+      CK_LAUNCH();
+    }
+    bound_features(a, sup, side == PBNG_SIDE_U ? G.u_off : G.v_off, nx, out);
+    CK(cudaStreamSynchronize(a.st));
   });
 }
 

@@ -160,8 +160,16 @@ struct TipParams {
   uint32_t n_bounds;
   int recount, compact, graph_rounds;
   uint64_t timeout_ns;
+  const float *mlp_params;  // learned bounds (bounds_mode == PBNG_BOUNDS_LEARNED)
+  uint32_t mlp_hidden, mlp_out;
+  std::vector<uint64_t> *bounds_used;  // optional record of theta(2..) used
 };
 void tip_decompose(Arena &a, Graph &G, int side, const TipParams &p, uint64_t *theta_out, pbng_stats *st);
+
+// ------------------------------------------------------- learned bounds
+uint64_t bound_features(Arena &a, const uint64_t *sup, const uint32_t *p_off, uint32_t nx, float *out128);
+std::vector<uint64_t> propose_bounds(Arena &a, const float *params, uint32_t hidden, uint32_t out, const float *feat,
+                                     uint64_t max_support);
 
 // ------------------------------------------------------------------ wing
 void wing_decompose(Arena &a, Graph &G, const TipParams &p, uint64_t *theta_out, pbng_stats *st);

@@ -428,6 +428,24 @@ __global__ void k_compact_list(const uint32_t *in, uint32_t n, const uint8_t *st
   }
 }
 
+// key range of the remaining vertices only (no work proxy)
+__global__ void k_keyrange(const uint32_t *alist, uint32_t na, const ull *sup, RangeState *rs) {
+  ull mn = ~0ull, mx = 0;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < na; j += (size_t)gridDim.x * blockDim.x) {
+    ull s = sup[alist[j]];
+    mn = min(mn, s);
+    mx = max(mx, s);
+  }
+  for (int o = 16; o; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&rs->kmin, mn);
+    atomicMax(&rs->kmax, mx);
+  }
+}
+
 // warp per remaining vertex: work proxy w = wedges of x on the current graph
 // (Sec. 3.2), key range and total work
 __global__ void k_weights(const uint32_t *alist, uint32_t na, const uint32_t *p_off, const uint32_t *p_adj,
@@ -856,6 +874,20 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     attr = true;
   }
 
+  // learned bounds: features of the initial supports -> MLP -> explicit bounds
+  std::vector<uint64_t> learned;
+  const uint64_t *bounds = prm.bounds;
+  uint32_t n_bounds = prm.n_bounds;
+  bool explicit_bounds = prm.bounds_mode == PBNG_BOUNDS_EXPLICIT;
+  if (prm.bounds_mode == PBNG_BOUNDS_LEARNED) {
+    float *feat = a.alloc<float>(128);
+    uint64_t K = bound_features(a, (const uint64_t *)sup, p_off, nx, feat);
+    learned = propose_bounds(a, prm.mlp_params, prm.mlp_hidden, prm.mlp_out, feat, K);
+    a.free(feat);
+    bounds = learned.data();
+    n_bounds = (uint32_t)learned.size();
+    explicit_bounds = true;
+  }
   uint32_t na = nx;
   uint32_t pi = 0;
   double scale = 1.0;
@@ -877,11 +909,24 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     bool last = pi + 1 >= P;
     CK(cudaMemsetAsync(rs, 0, sizeof(RangeState), a.st));
     set_u64(a, (uint64_t *)&rs->kmin, ~0ull);
-    k_weights<<<grid_for((size_t)na * 32, T, cap), T, 0, a.st>>>(alist, na, p_off, p_adj, o_len, sup, wl, rs);
-    CK_LAUNCH();
+    // the work proxy is only needed when find_range will run
+    bool given = last || (explicit_bounds && pi < n_bounds);
     ull hk[3];
-    CK(cudaMemcpyAsync(hk, &rs->kmin, sizeof(hk), cudaMemcpyDeviceToHost, a.st));
-    CK(cudaStreamSynchronize(a.st));
+    if (given) {
+      k_keyrange<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, sup, rs);
+      CK_LAUNCH();
+      CK(cudaMemcpyAsync(hk, &rs->kmin, sizeof(hk), cudaMemcpyDeviceToHost, a.st));
+      CK(cudaStreamSynchronize(a.st));
+      given = last || bounds[pi] > hk[0];
+    }
+    if (!given) {
+      CK(cudaMemsetAsync(rs, 0, sizeof(RangeState), a.st));
+      set_u64(a, (uint64_t *)&rs->kmin, ~0ull);
+      k_weights<<<grid_for((size_t)na * 32, T, cap), T, 0, a.st>>>(alist, na, p_off, p_adj, o_len, sup, wl, rs);
+      CK_LAUNCH();
+      CK(cudaMemcpyAsync(hk, &rs->kmin, sizeof(hk), cudaMemcpyDeviceToHost, a.st));
+      CK(cudaStreamSynchronize(a.st));
+    }
     ull kmin = hk[0], kmax = hk[1], wsum = hk[2];
     // adaptive target (Sec. 3.1.3): remaining work over remaining partitions,
     // scaled by how far the previous partition overshot its estimate
@@ -895,8 +940,8 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     if (last) {
       thi = ~0ull;
       use_est = false;
-    } else if (prm.bounds_mode == PBNG_BOUNDS_EXPLICIT && pi < prm.n_bounds && prm.bounds[pi] > kmin) {
-      thi = prm.bounds[pi];
+    } else if (explicit_bounds && pi < n_bounds && bounds[pi] > kmin) {
+      thi = bounds[pi];
       use_est = false;
     }
     uint64_t init_est = 0;
@@ -915,6 +960,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     }
     prev_init_est = init_est;
     cur_final = 0;
+    if (prm.bounds_used && !last) prm.bounds_used->push_back(thi);
     // ---- snapshot + first active set (Alg. 4 l.6-9)
     CK(cudaMemsetAsync(dc, 0, 4, a.st));
     k_scan_frontier<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, sup, init, &rs->theta_hi, 1, front, dc);

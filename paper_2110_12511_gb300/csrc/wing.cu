@@ -870,6 +870,7 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
       set_u64(a, (uint64_t *)&rs->theta_hi, thi);
     }
     prev_init_est = init_est;
+    if (prm.bounds_used && !last) prm.bounds_used->push_back(thi);
     CK(cudaMemsetAsync(dc, 0, 4, a.st));
     k_wing_scan<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, sup, init, (const ull *)&rs->theta_hi, front, dc);
     CK_LAUNCH();
