@@ -268,8 +268,11 @@ def main():
     ap.add_argument("--impl", default="pbng", choices=["pbng", "reference"])
     ap.add_argument("--P", type=int, default=150)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer run (profiling)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--graph-rounds", action="store_true", help="coarse rounds as a CUDA graph with a device loop")
+    ap.add_argument("--no-recount", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_info()
     if args.impl == "reference":
@@ -298,9 +301,11 @@ def main():
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
+    kw = {"graph_rounds": args.graph_rounds, "recount": not args.no_recount}
+
     def step():
-        su = pbng.tip_decompose(dg, "U", P=args.P, with_stats=True)[1]
-        sv = pbng.tip_decompose(dg, "V", P=args.P, with_stats=True)[1]
+        su = pbng.tip_decompose(dg, "U", P=args.P, with_stats=True, **kw)[1]
+        sv = pbng.tip_decompose(dg, "V", P=args.P, with_stats=True, **kw)[1]
         return su, sv
 
     for _ in range(args.warmup):
@@ -364,21 +369,22 @@ def main():
         u_adj = pin_adj.numpy().view(np.uint32)
 
     hg = HostG()
-    pbng.tip_decompose_host(hg, "U", P=args.P)
     e2e_t = []
     e2e_w = 0
-    for _ in range(max(1, args.steps)):
+    if not args.no_e2e:
+        pbng.tip_decompose_host(hg, "U", P=args.P, **kw)
+    for _ in range(0 if args.no_e2e else max(1, args.steps)):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        _, su = pbng.tip_decompose_host(hg, "U", P=args.P, with_stats=True)
-        _, sv = pbng.tip_decompose_host(hg, "V", P=args.P, with_stats=True)
+        _, su = pbng.tip_decompose_host(hg, "U", P=args.P, with_stats=True, **kw)
+        _, sv = pbng.tip_decompose_host(hg, "V", P=args.P, with_stats=True, **kw)
         e2e_t.append(time.perf_counter() - t0)
         e2e_w += tip_wedges(su) + tip_wedges(sv)
     tt = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
     if ws > 1:
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_value = ws * e2e_w / float(tt.item())
+    e2e_value = ws * e2e_w / float(tt.item()) if e2e_t else None
     h2d = 2 * ((g.nu + 1) * 8 + g.m * 4)
     d2h = (g.nu + g.nv) * 8
 
@@ -398,6 +404,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic (seeded Chung-Lu generator)",
             "config": {"workload": WORKLOAD_DESC, "name": WORKLOAD, "P": args.P, "sides": "U,V",
+                       "graph_rounds": args.graph_rounds, "recount": not args.no_recount,
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write)", "nu": g.nu, "nv": g.nv, "m": g.m,
                        "wedges_per_step": wedges_step,
@@ -408,7 +415,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "wedges/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": 1000 * sum(e2e_t) / len(e2e_t)},
+                    "ms_per_step": 1000 * sum(e2e_t) / len(e2e_t) if e2e_t else None},
             "gpu_launches": int(sum(s["launches"] for st in stats for s in st)),
             "clocks": clk.summary(),
         }

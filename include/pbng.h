@@ -70,8 +70,10 @@ typedef struct pbng_opts {
   int recount;             /* 1 (default): batch re-count when cheaper than peeling (Sec. 5.1) */
   int compact;             /* 1 (default): dynamic graph updates (Sec. 5.2) */
   int mem;                 /* PBNG_MEM_DEVICE (default) or PBNG_MEM_HOST */
-  int graph_rounds;        /* 1: coarse-phase rounds run as a captured CUDA graph with a
-                              device-side loop (no host round trip per round); default 0 */
+  int graph_rounds;        /* tip only. 1: the coarse-phase rounds of each range run as one
+                              CUDA graph whose conditional WHILE node loops on the device
+                              (no host round trip per round); every round peels, so
+                              `recount` is not used; results are identical.  Default 0 */
   uint64_t timeout_ns;     /* limit for bounded device waits; 0 = 10 s */
   void *stream;            /* cudaStream_t */
   const float *mlp_params; /* LEARNED (tip): device float32 parameters, layout of pbng_mlp_forward,

@@ -274,7 +274,7 @@ def tip_decompose_host(g, side="U", P=150, with_stats=False, **kw):
     n = g.nu if s == SIDE_U else g.nv
     out = np.zeros(max(n, 1), dtype=np.uint64)
     o = _opts(kw.get("stream"), kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), mem=MEM_HOST,
-              keep=[])
+              graph_rounds=kw.get("graph_rounds", False), keep=[])
     st = Stats()
     cg = Bigraph(int(g.nu), int(g.nv), adj.size, off.ctypes.data, adj.ctypes.data if adj.size else 0)
     rc = lib().pbng_tip_decompose(ctypes.byref(cg), s, int(P), out.ctypes.data, ctypes.byref(o), ctypes.byref(st))

@@ -321,7 +321,7 @@ size_t block_smem(int kind) {
 void count_butterflies(Arena &a, const Graph &G, const CountOut &o) {
   if (!G.has_labels) fail(PBNG_EINVAL, "internal: labelled adjacency missing");
   if (G.m == 0 || G.n == 0) return;
-  CArgs A;
+  CArgs A{};
   A.off = G.lab_off;
   A.adj = G.lab_adj;
   A.eid = G.lab_eid;

@@ -32,14 +32,17 @@ namespace {
 
 enum : uint8_t { ST_ALIVE = 0, ST_ACTIVE = 1, ST_PEELED = 2 };
 
-constexpr uint32_t PW_MAXW = 256, PW_CAP = 512;  // warp-per-vertex, shared hash
+constexpr uint32_t PW_MAXW = 256, PW_CAP = 512;  // fine phase: warp-per-vertex shared hash
+constexpr uint32_t QW_MAXW = 512, QW_CAP = 1024;  // coarse peel: warp-per-vertex shared hash
+constexpr uint32_t QG_MAXW = 2048, QG_CAP = 4096; // coarse peel: 256-thread group per vertex
+constexpr int QGT = 256;                          // threads of a group
 constexpr uint32_t PB_CAP = 8192;                // block-per-vertex shared hash slots (64 KB)
 constexpr uint32_t PB_FILL = PB_CAP / 2;         // most distinct targets a hash pass may hold
 constexpr uint32_t P_CHUNK = 2 * PB_CAP;         // block-per-vertex dense counters (same 64 KB)
 constexpr int PB_PER_SM = 3;                     // resident blocks per SM (shared memory bound)
 constexpr uint32_t P_DENSE = 16384;              // fine phase: dense shared counters when |X_p| <= this
 constexpr int PBT = 512, PWT = 256;
-enum { PC_WARP = 0, PC_BLOCK = 1, PNCLASS = 2 };
+enum { PC_WARP = 0, PC_GROUP = 1, PC_BLOCK = 2, PNCLASS = 3 };
 static_assert(P_CHUNK <= 2 * PB_CAP, "dense counters share the hash table memory");
 
 using ull = unsigned long long;
@@ -61,6 +64,42 @@ template <int N>
 struct PMid {
   uint32_t lo[N];
   uint32_t pre[N + 1];
+};
+
+// NT threads of a block (warps base/32 .. ) synchronised by a named barrier
+template <int NT>
+struct SubGrp {
+  static constexpr int N = NT;
+  int base, bar;
+  uint32_t *ws;  // NT/32 + 2 words of shared scratch
+  __device__ __forceinline__ int rank() const { return (int)threadIdx.x - base; }
+  __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(NT) : "memory"); }
+  __device__ __forceinline__ uint32_t scan(uint32_t x, uint32_t *pre) const {
+    int r = rank(), l = r & 31, w = r >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (l >= o) inc += y;
+    }
+    if (l == 31) ws[w] = inc;
+    sync();
+    if (w == 0) {
+      uint32_t s = l < NT / 32 ? ws[l] : 0u, si = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, si, o);
+        if (l >= o) si += y;
+      }
+      if (l < NT / 32) ws[l] = si - s;
+      if (l == NT / 32 - 1) ws[NT / 32] = si;
+    }
+    sync();
+    pre[r] = inc - x + ws[w];
+    if (r == 0) pre[NT] = ws[NT / 32];
+    sync();
+    return pre[NT];
+  }
 };
 
 template <class Grp, int N>
@@ -116,8 +155,9 @@ struct PHash {
   }
 };
 
+// returns this thread's number of support updates
 template <class Grp, int N, class Tbl>
-__device__ void peel_vertex(const PeelArgs &A, uint32_t x, const Grp &g, PMid<N> &mb, const Tbl &tbl, uint64_t thi) {
+__device__ uint64_t peel_vertex(const PeelArgs &A, uint32_t x, const Grp &g, PMid<N> &mb, const Tbl &tbl, uint64_t thi) {
   uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
   for (uint32_t base = 0; base < xd; base += N) {
     uint32_t T = peel_load(A, xo, xd, base, g, mb);
@@ -126,8 +166,12 @@ __device__ void peel_vertex(const PeelArgs &A, uint32_t x, const Grp &g, PMid<N>
   }
   uint64_t nup = tbl.drain(A, xo, xd, g, mb, thi);
   g.sync();
-  uint64_t t = g.sum64(nup);
-  if (g.rank() == 0 && t && A.updates) atomicAdd(A.updates, (ull)t);
+  return nup;
+}
+
+__device__ __forceinline__ void add_updates(const PeelArgs &A, uint64_t nup) {
+  for (int o = 16; o; o >>= 1) nup += __shfl_xor_sync(0xffffffffu, nup, o);
+  if ((threadIdx.x & 31) == 0 && nup && A.updates) atomicAdd(A.updates, (ull)nup);
 }
 
 // Slice of y's current list holding target ids in [c0, c1) (lists are sorted).
@@ -185,8 +229,8 @@ struct ZHash {
 // typical range fills the hash, and widths adapt to the observed density.
 // Each aggregated target x' that is still unpeeled loses C(c(x,x'), 2).
 template <int N>
-__device__ void peel_vertex_block(const PeelArgs &A, uint32_t x, uint32_t W, const BlockGrp<N> &g, PMid<N> &mb,
-                                  uint32_t *tab, uint64_t thi) {
+__device__ uint64_t peel_vertex_block(const PeelArgs &A, uint32_t x, uint32_t W, const BlockGrp<N> &g, PMid<N> &mb,
+                                      uint32_t *tab, uint64_t thi) {
   uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
   uint64_t nup = 0;
   uint32_t width;
@@ -272,31 +316,60 @@ __device__ void peel_vertex_block(const PeelArgs &A, uint32_t x, uint32_t W, con
     c0 = c1;
     if (T < PB_FILL / 4 && width < A.nx / 2) width *= 2;
   }
-  uint64_t t = g.sum64(nup);
-  if (g.rank() == 0 && t && A.updates) atomicAdd(A.updates, (ull)t);
+  return nup;
 }
 
 __global__ void __launch_bounds__(PWT) k_peel_warp(PeelArgs A, const uint64_t *list, const unsigned *count) {
   extern __shared__ __align__(16) uint8_t sm[];
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr size_t per = align16(PW_CAP * 8 + sizeof(PMid<32>));
-  uint32_t *key = (uint32_t *)(sm + w * per), *val = key + PW_CAP;
-  PMid<32> &mb = *(PMid<32> *)(sm + w * per + PW_CAP * 8);
-  for (uint32_t i = lane; i < PW_CAP; i += 32) key[i] = EMPTY_KEY, val[i] = 0;
+  constexpr size_t per = align16(QW_CAP * 8 + sizeof(PMid<32>));
+  uint32_t *key = (uint32_t *)(sm + w * per), *val = key + QW_CAP;
+  PMid<32> &mb = *(PMid<32> *)(sm + w * per + QW_CAP * 8);
+  for (uint32_t i = lane; i < QW_CAP; i += 32) key[i] = EMPTY_KEY, val[i] = 0;
   __syncwarp();
   WarpGrp g;
-  uint64_t thi = *A.theta_hi;
+  uint64_t thi = *A.theta_hi, nup = 0;
   unsigned n = *count;
   for (size_t it = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; it < n; it += ((size_t)gridDim.x * blockDim.x) >> 5) {
     uint64_t item = list[it];
     uint32_t x = (uint32_t)item, W = (uint32_t)(item >> 32);
     uint32_t cap = pow2_at_least(max(2u * W, 32u));
     PHash p{SmemHash{key, val, cap - 1}, cap};
-    peel_vertex(A, x, g, mb, p, thi);
+    nup += peel_vertex(A, x, g, mb, p, thi);
   }
+  add_updates(A, nup);
 }
 
+// two 256-thread groups per block, each with its own shared hash and named
+// barrier, one active vertex per group
+__global__ void __launch_bounds__(2 * QGT) k_peel_group(PeelArgs A, const uint64_t *list, const unsigned *count) {
+  if ((size_t)blockIdx.x * 2 >= *count) return;  // fixed grids of graph-captured rounds
+  extern __shared__ __align__(16) uint8_t sm[];
+  int sub = threadIdx.x / QGT;
+  constexpr size_t per = align16(QG_CAP * 8 + sizeof(PMid<QGT>) + (QGT / 32 + 2) * 4);
+  uint8_t *base = sm + sub * per;
+  uint32_t *key = (uint32_t *)base, *val = key + QG_CAP;
+  PMid<QGT> &mb = *(PMid<QGT> *)(base + QG_CAP * 8);
+  uint32_t *ws = (uint32_t *)(base + QG_CAP * 8 + sizeof(PMid<QGT>));
+  SubGrp<QGT> g{sub * QGT, 1 + sub, ws};
+  for (uint32_t i = g.rank(); i < QG_CAP; i += QGT) key[i] = EMPTY_KEY, val[i] = 0;
+  g.sync();
+  uint64_t thi = *A.theta_hi, nup = 0;
+  unsigned n = *count;
+  for (size_t it = (size_t)blockIdx.x * 2 + sub; it < n; it += (size_t)gridDim.x * 2) {
+    uint64_t item = list[it];
+    uint32_t x = (uint32_t)item, W = (uint32_t)(item >> 32);
+    uint32_t cap = pow2_at_least(max(2u * W, 64u));
+    PHash p{SmemHash{key, val, cap - 1}, cap};
+    nup += peel_vertex(A, x, g, mb, p, thi);
+  }
+  add_updates(A, nup);
+}
+
+size_t peel_group_smem() { return 2 * align16(QG_CAP * 8 + sizeof(PMid<QGT>) + (QGT / 32 + 2) * 4); }
+
 __global__ void __launch_bounds__(PBT) k_peel_block(PeelArgs A, const uint64_t *list, const unsigned *count) {
+  if (blockIdx.x >= *count) return;  // fixed grids of graph-captured rounds
   extern __shared__ __align__(16) uint8_t sm[];
   PMid<PBT> &mb = *(PMid<PBT> *)sm;
   constexpr size_t o1 = align16(sizeof(PMid<PBT>));
@@ -306,12 +379,13 @@ __global__ void __launch_bounds__(PBT) k_peel_block(PeelArgs A, const uint64_t *
   BlockGrp<PBT> g{ws, ws64};
   for (uint32_t i = threadIdx.x; i < 2 * PB_CAP; i += PBT) tab[i] = 0;  // empty hash == zero counters
   __syncthreads();
-  uint64_t thi = *A.theta_hi;
+  uint64_t thi = *A.theta_hi, nup = 0;
   unsigned n = *count;
   for (size_t it = blockIdx.x; it < n; it += gridDim.x) {
     uint64_t item = list[it];
-    peel_vertex_block(A, (uint32_t)item, (uint32_t)(item >> 32), g, mb, tab, thi);
+    nup += peel_vertex_block(A, (uint32_t)item, (uint32_t)(item >> 32), g, mb, tab, thi);
   }
+  add_updates(A, nup);
 }
 
 size_t peel_block_smem() { return align16(sizeof(PMid<PBT>)) + 256 + (size_t)PB_CAP * 8; }
@@ -328,17 +402,34 @@ struct PrepArgs {
   uint64_t *lists;  // PNCLASS x nx
   unsigned *counts;
   uint32_t nx;
+  // dynamic graph updates (Sec. 5.2): the active vertices' entries die this
+  // round; a Y list is queued for compaction once a quarter of it is dead
+  int compact;
+  uint32_t *dead, *ytouch, *touched;
+  unsigned *touched_n;
+  const unsigned *nf_dev = nullptr, *pi_dev = nullptr;  // device-resident sizes (graph-captured rounds)
 };
 
 // one warp per active vertex: partition id, wedge count, class, touched Y lists
 __global__ void k_prep(PrepArgs A) {
   int lane = threadIdx.x & 31;
   size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  if (A.nf_dev) {
+    A.nf = *A.nf_dev;
+    A.pi = *A.pi_dev;
+  }
   for (size_t j = gw; j < A.nf; j += nw) {
     uint32_t x = A.frontier[j];
     uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
     uint64_t W = 0;
-    for (uint32_t k = lane; k < xd; k += 32) W += A.o_len[A.p_adj[xo + k]];
+    for (uint32_t k = lane; k < xd; k += 32) {
+      uint32_t y = A.p_adj[xo + k], len = A.o_len[y];
+      W += len;
+      if (A.compact) {
+        uint32_t d = atomicAdd(&A.dead[y], 1u) + 1;
+        if (4 * d >= len && atomicExch(&A.ytouch[y], 1u) == 0u) A.touched[atomicAdd(A.touched_n, 1u)] = y;
+      }
+    }
 #pragma unroll
     for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
     if (lane == 0) {
@@ -347,7 +438,7 @@ __global__ void k_prep(PrepArgs A) {
       atomicAdd(&A.sum_w[0], (ull)W);
       atomicAdd(&A.sum_w[1], (ull)xd);
       if (W >= 2) {
-        int c = W <= PW_MAXW ? PC_WARP : PC_BLOCK;
+        int c = W <= QW_MAXW ? PC_WARP : (W <= QG_MAXW ? PC_GROUP : PC_BLOCK);
         unsigned p = atomicAdd(&A.counts[c], 1u);
         A.lists[(size_t)c * A.nx + p] = (uint64_t)x | ((uint64_t)min(W, (uint64_t)0xffffffffu) << 32);
       }
@@ -355,31 +446,45 @@ __global__ void k_prep(PrepArgs A) {
   }
 }
 
-// warp per peeled vertex: mark it, and count the dead entries it leaves in
-// the Y-side lists; a list is queued for compaction (dynamic graph update,
-// Sec. 5.2) once a quarter of it is dead, so each entry is scanned O(1) times
-// by compaction overall.
 __global__ void k_mark_peeled(const uint32_t *f, uint32_t nf, uint8_t *state, uint8_t *lab_alive, const uint32_t *x2lab,
-                              const uint32_t *p_off, const uint32_t *p_adj, const uint32_t *o_len, uint32_t *dead,
-                              uint32_t *ytouch, uint32_t *touched, unsigned *touched_n, int compact) {
-  int lane = threadIdx.x & 31;
-  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
-  for (size_t j = gw; j < nf; j += nw) {
+                              const unsigned *nf_dev = nullptr) {
+  if (nf_dev) nf = *nf_dev;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < nf; j += (size_t)gridDim.x * blockDim.x) {
     uint32_t x = f[j];
-    if (lane == 0) {
-      state[x] = ST_PEELED;
-      if (lab_alive) lab_alive[x2lab[x]] = 0;
-    }
-    if (!compact) continue;
-    uint32_t xo = p_off[x], xd = p_off[x + 1] - xo;
-    for (uint32_t k = lane; k < xd; k += 32) {
-      uint32_t y = p_adj[xo + k];
-      uint32_t d = atomicAdd(&dead[y], 1u) + 1;
-      if (4 * d >= o_len[y] && atomicExch(&ytouch[y], 1u) == 0u) {
-        unsigned p = atomicAdd(touched_n, 1u);
-        touched[p] = y;
-      }
-    }
+    state[x] = ST_PEELED;
+    if (lab_alive) lab_alive[x2lab[x]] = 0;
+  }
+}
+
+// device-resident state of the graph-captured coarse rounds
+struct RoundDev {
+  unsigned nf, nn, touched_n, pi;
+  unsigned counts[4];
+  ull sum_w[2];
+  ull tot_wedges, tot_exp, tot_front, rounds, part_work, iters;
+};
+
+__global__ void k_round_reset(RoundDev *R) {
+  R->nn = 0;
+  R->touched_n = 0;
+  for (int i = 0; i < 4; i++) R->counts[i] = 0;
+  R->sum_w[0] = R->sum_w[1] = 0;
+}
+
+// end of one round: totals, next frontier size, and (last round of the body)
+// the loop condition of the conditional node
+__global__ void k_round_end(RoundDev *R, cudaGraphConditionalHandle h, int set_cond) {
+  if (R->nf) {
+    R->rounds++;
+    R->tot_wedges += R->sum_w[0];
+    R->tot_exp += R->sum_w[1];
+    R->tot_front += R->nf;
+    R->part_work += R->sum_w[0];
+  }
+  R->nf = R->nn;
+  if (set_cond) {
+    R->iters++;
+    cudaGraphSetConditional(h, R->nn > 0 ? 1u : 0u);
   }
 }
 
@@ -853,7 +958,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   RangeState *rs = a.zeros<RangeState>(1);
   ull *wl = a.alloc<ull>(nx);
 
-  PeelArgs PA;
+  PeelArgs PA{};
   PA.p_off = p_off;
   PA.p_adj = p_adj;
   PA.o_off = o_off;
@@ -866,13 +971,87 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   PA.nx = nx;
 
   static bool attr = false;
-  size_t wsm = (PWT / 32) * align16(PW_CAP * 8 + sizeof(PMid<32>));
+  size_t wsm = (PWT / 32) * align16(QW_CAP * 8 + sizeof(PMid<32>));
   if (!attr) {
     CK(cudaFuncSetAttribute(k_peel_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
     CK(cudaFuncSetAttribute(k_peel_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)peel_block_smem()));
+    CK(cudaFuncSetAttribute(k_peel_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)peel_group_smem()));
     CK(cudaFuncSetAttribute(k_fd_tip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fd_smem()));
     attr = true;
   }
+
+  // graph-captured coarse rounds: the rounds of one range run as a CUDA graph
+  // with a conditional WHILE node (two rounds per body, ping-pong frontier
+  // buffers); every size is read from device memory, so there is no host
+  // round trip per round.  The re-count branch needs host-side bucketing of
+  // its starts, so this mode peels every round.
+  struct GraphHold {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t e = nullptr;
+    ~GraphHold() {
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
+    }
+  } gh;
+  bool use_graph = prm.graph_rounds != 0;
+  RoundDev *Rd = use_graph ? a.zeros<RoundDev>(1) : nullptr;
+  auto build_round_graph = [&]() {
+    CK(cudaGraphCreate(&gh.g, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, gh.g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, gh.g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // capture on a private stream (the caller's may be the legacy default stream)
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    for (int half = 0; half < 2; half++) {
+      uint32_t *F = half == 0 ? front : front2, *Nx = half == 0 ? front2 : front;
+      k_round_reset<<<1, 1, 0, cs>>>(Rd);
+      PrepArgs R{};
+      R.frontier = F;
+      R.nf = 0;
+      R.p_off = p_off;
+      R.p_adj = p_adj;
+      R.o_len = o_len;
+      R.part = part;
+      R.pi = 0;
+      R.state = state;
+      R.sum_w = Rd->sum_w;
+      R.lists = plists;
+      R.counts = Rd->counts;
+      R.nx = nx;
+      R.compact = prm.compact;
+      R.dead = dead;
+      R.ytouch = ytouch;
+      R.touched = touched;
+      R.touched_n = &Rd->touched_n;
+      R.nf_dev = &Rd->nf;
+      R.pi_dev = &Rd->pi;
+      k_prep<<<16 * sms, T, 0, cs>>>(R);
+      PeelArgs P2 = PA;
+      P2.next = Nx;
+      P2.next_n = &Rd->nn;
+      k_peel_warp<<<6 * sms, PWT, wsm, cs>>>(P2, plists + (size_t)PC_WARP * nx, Rd->counts + PC_WARP);
+      k_peel_group<<<3 * sms, 2 * QGT, peel_group_smem(), cs>>>(P2, plists + (size_t)PC_GROUP * nx, Rd->counts + PC_GROUP);
+      k_peel_block<<<PB_PER_SM * sms, PBT, peel_block_smem(), cs>>>(P2, plists + (size_t)PC_BLOCK * nx, Rd->counts + PC_BLOCK);
+      k_mark_peeled<<<8 * sms, T, 0, cs>>>(F, 0, state, lab_alive, x2lab, &Rd->nf);
+      if (prm.compact) k_compact<<<4 * sms, T, 0, cs>>>(touched, &Rd->touched_n, o_off, o_adj, o_len, ytouch, dead, state);
+      k_round_end<<<1, 1, 0, cs>>>(Rd, h, half == 1);
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t le = cudaGetLastError(), ce = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    CK(le);
+    CK(ce);
+    CK(cudaGraphInstantiate(&gh.e, gh.g, 0));
+  };
 
   // learned bounds: features of the initial supports -> MLP -> explicit bounds
   std::vector<uint64_t> learned;
@@ -962,6 +1141,32 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     cur_final = 0;
     if (prm.bounds_used && !last) prm.bounds_used->push_back(thi);
     // ---- snapshot + first active set (Alg. 4 l.6-9)
+    if (use_graph) {
+      // this range's rounds run entirely on the device; the host reads the
+      // totals once the range is done (its work feeds the next target)
+      RoundDev hr;
+      CK(cudaMemsetAsync(&Rd->nf, 0, 8, a.st));  // nf, nn
+      CK(cudaMemsetAsync(&Rd->part_work, 0, 8, a.st));
+      CK(cudaMemcpyAsync(&Rd->pi, &pi, 4, cudaMemcpyHostToDevice, a.st));
+      k_scan_frontier<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, sup, init, &rs->theta_hi, 1, front, &Rd->nf);
+      CK_LAUNCH();
+      if (!gh.e) build_round_graph();
+      ull it0 = 0;
+      CK(cudaMemcpyAsync(&it0, &Rd->iters, 8, cudaMemcpyDeviceToHost, a.st));
+      g_prof.begin(PROF_PEEL);
+      CK(cudaGraphLaunch(gh.e, a.st));
+      g_prof.end();
+      CK(cudaMemcpyAsync(&hr, Rd, sizeof(RoundDev), cudaMemcpyDeviceToHost, a.st));
+      CK(cudaStreamSynchronize(a.st));
+      cur_final = hr.part_work;
+      g_launches += (hr.iters - it0) * 2 * (prm.compact ? 8 : 7);
+      rounds = hr.rounds;
+      wedges_cd = hr.tot_wedges;
+      exp_cd = hr.tot_exp;
+      front_cd = hr.tot_front;
+      pi++;
+      continue;
+    }
     CK(cudaMemsetAsync(dc, 0, 4, a.st));
     k_scan_frontier<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, sup, init, &rs->theta_hi, 1, front, dc);
     CK_LAUNCH();
@@ -971,7 +1176,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       rounds++;
       CK(cudaMemsetAsync(dc + 1, 0, 6 * 4, a.st));
       CK(cudaMemsetAsync(sumw, 0, 16, a.st));
-      PrepArgs R;
+      PrepArgs R{};
       R.frontier = front;
       R.nf = nf;
       R.p_off = p_off;
@@ -984,6 +1189,11 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       R.lists = plists;
       R.counts = dc + 3;
       R.nx = nx;
+      R.compact = prm.compact;
+      R.dead = dead;
+      R.ytouch = ytouch;
+      R.touched = touched;
+      R.touched_n = dc + 2;
       k_prep<<<grid_for((size_t)nf * 32, T, cap), T, 0, a.st>>>(R);
       CK_LAUNCH();
       unsigned hc[6];
@@ -997,8 +1207,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       if (do_recount) {
         // Sec. 5.1: re-count the remaining vertices instead of peeling
         recounts++;
-        k_mark_peeled<<<grid_for((size_t)nf * 32, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab, p_off, p_adj,
-                                                                          o_len, dead, ytouch, touched, dc + 2, prm.compact);
+        k_mark_peeled<<<grid_for(nf, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab);
         CK_LAUNCH();
         CK(cudaMemsetAsync(cnt_lab, 0, (size_t)G.n * 8, a.st));
         CountOut rc;
@@ -1022,14 +1231,18 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
                                                                                                 dc + 3 + PC_WARP);
           CK_LAUNCH();
         }
+        if (hc[2 + PC_GROUP]) {
+          k_peel_group<<<std::min<unsigned>((hc[2 + PC_GROUP] + 1) / 2, 3 * sms), 2 * QGT, peel_group_smem(), a.st>>>(
+              PA, plists + (size_t)PC_GROUP * nx, dc + 3 + PC_GROUP);
+          CK_LAUNCH();
+        }
         if (hc[2 + PC_BLOCK]) {
           k_peel_block<<<std::min<unsigned>(hc[2 + PC_BLOCK], PB_PER_SM * sms), PBT, peel_block_smem(), a.st>>>(
               PA, plists + (size_t)PC_BLOCK * nx, dc + 3 + PC_BLOCK);
           CK_LAUNCH();
         }
         g_prof.end();
-        k_mark_peeled<<<grid_for((size_t)nf * 32, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab, p_off, p_adj,
-                                                                          o_len, dead, ytouch, touched, dc + 2, prm.compact);
+        k_mark_peeled<<<grid_for(nf, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab);
         CK_LAUNCH();
       }
       if (prm.compact) {
@@ -1090,7 +1303,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
 
   // support initialisation vector (Sec. 3.1.1) -> fine-phase supports
   CK(cudaMemcpyAsync(sup, init, (size_t)nx * 8, cudaMemcpyDeviceToDevice, a.st));
-  FDArgs F;
+  FDArgs F{};
   F.p_off = p_off;
   F.p_adj = p_adj;
   F.o_off = o_off;

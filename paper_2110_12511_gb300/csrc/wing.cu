@@ -713,7 +713,7 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   uint32_t *k0 = a.alloc<uint32_t>((size_t)nb + 1), *boff = a.alloc<uint32_t>((size_t)nb + 1);
   uint32_t *pe1 = a.alloc<uint32_t>(np + 1), *pe2 = a.alloc<uint32_t>(np + 1), *pbloom = a.alloc<uint32_t>(np + 1);
   if (np) {
-    FillArgs F;
+    FillArgs F{};
     F.off = G.lab_off;
     F.adj = G.lab_adj;
     F.eid = G.lab_eid;
@@ -799,7 +799,7 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   ull *wctr = a.zeros<ull>(8);  // [0] CD links, [1] CD updates, [4] FD links, [5] FD updates, [6] FD steps
   RangeState *rs = a.zeros<RangeState>(1);
   ull *wl = a.alloc<ull>(m);
-  CDArgs A;
+  CDArgs A{};
   A.pe1 = pe1;
   A.pe2 = pe2;
   A.pbloom = pbloom;
@@ -966,7 +966,7 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   k_fd_reset<<<grid_for(std::max(np, (size_t)m), T, cap), T, 0, a.st>>>(palive, np, state, m);
   CK_LAUNCH();
   uint32_t *gcnt = a.zeros<uint32_t>((size_t)ngroups + 1), *gtouch = a.alloc<uint32_t>(2 * (size_t)ngroups + 2);
-  WFDArgs W;
+  WFDArgs W{};
   W.pe1 = pe1;
   W.pe2 = pe2;
   W.eoff = eoff;

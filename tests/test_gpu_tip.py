@@ -102,6 +102,31 @@ def test_tip_optimisations_do_not_change_results(pbng, recount, compact):
         assert np.array_equal(got, oracle_tip(name, side))
 
 
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("side", ["U", "V"])
+def test_tip_graph_rounds_match_oracle(pbng, name, side):
+    """Coarse rounds captured as a CUDA graph with a device-side WHILE loop."""
+    dg = pbng.to_device(GRAPHS[name])
+    for P in (1, 8, 150):
+        got = pbng.as_u64(pbng.tip_decompose(dg, side, P=P, graph_rounds=True))
+        assert np.array_equal(got, oracle_tip(name, side))
+
+
+@pytest.mark.parametrize("compact", [False, True])
+def test_tip_graph_rounds_same_work_as_host_loop(pbng, compact):
+    """Without re-count both modes peel the same rounds with the same wedges."""
+    name = "chunglu_20k_4k_200k"
+    dg = pbng.to_device(GRAPHS[name])
+    for side in ("U", "V"):
+        a, sa = pbng.tip_decompose(dg, side, P=40, recount=False, compact=compact, with_stats=True)
+        b, sb = pbng.tip_decompose(dg, side, P=40, recount=False, compact=compact, graph_rounds=True,
+                                   with_stats=True)
+        assert np.array_equal(pbng.as_u64(a), pbng.as_u64(b))
+        assert np.array_equal(pbng.as_u64(b), oracle_tip(name, side))
+        for k in ("rounds", "wedges_cd", "parts_used", "updates"):
+            assert sa[k] == sb[k], k
+
+
 def test_tip_explicit_and_random_bounds(pbng):
     name = "chunglu_20k_4k_200k"
     g = GRAPHS[name]
