@@ -83,6 +83,9 @@ typedef struct pbng_opts {
                               actually used (the last, unbounded range is not listed) */
   uint32_t n_bounds_out;   /* capacity of bounds_out; the count written is stats->parts_used - 1
                               (at most this many are stored) */
+  uint32_t bucket_shift;   /* tip: the coarse peel cuts the peeled side's ids into buckets of
+                              2^bucket_shift ids (at most 512 buckets); 0 (default) = automatic,
+                              else 14..30 (raised when needed); results are identical */
 } pbng_opts;
 
 typedef struct pbng_stats {

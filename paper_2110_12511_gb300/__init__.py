@@ -37,7 +37,8 @@ class Opts(ctypes.Structure):
                 ("recount", ctypes.c_int), ("compact", ctypes.c_int), ("mem", ctypes.c_int),
                 ("graph_rounds", ctypes.c_int), ("timeout_ns", ctypes.c_uint64), ("stream", ctypes.c_void_p),
                 ("mlp_params", ctypes.c_void_p), ("mlp_hidden", ctypes.c_uint32), ("mlp_out", ctypes.c_uint32),
-                ("bounds_out", ctypes.c_void_p), ("n_bounds_out", ctypes.c_uint32)]
+                ("bounds_out", ctypes.c_void_p), ("n_bounds_out", ctypes.c_uint32),
+                ("bucket_shift", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -145,9 +146,10 @@ def to_device(g, device="cuda") -> DeviceGraph:
 
 
 def _opts(stream=None, bounds=None, recount=True, compact=True, mem=MEM_DEVICE, graph_rounds=False, keep=None,
-          mlp=None, bounds_out=None):
+          mlp=None, bounds_out=None, bucket_shift=0):
     o = Opts()
     lib().pbng_opts_init(ctypes.byref(o))
+    o.bucket_shift = int(bucket_shift)
     o.recount = int(bool(recount))
     o.compact = int(bool(compact))
     o.mem = mem
@@ -205,7 +207,7 @@ def _side(side) -> int:
 
 
 def tip_decompose(dg: DeviceGraph, side="U", P=150, bounds=None, recount=True, compact=True, graph_rounds=False,
-                  stream=None, with_stats=False, mlp=None, bounds_out=None):
+                  stream=None, with_stats=False, mlp=None, bounds_out=None, bucket_shift=0):
     """Tip numbers of one side (two-phase PBNG, Sec. 3.1-3.2).
 
     bounds: explicit upper bounds; mlp: (params, hidden, out) of the learned
@@ -215,7 +217,8 @@ def tip_decompose(dg: DeviceGraph, side="U", P=150, bounds=None, recount=True, c
     n = dg.nu if s == SIDE_U else dg.nv
     out = torch.empty(max(n, 1), dtype=torch.int64, device=dg.u_off.device)
     keep = []
-    o = _opts(stream, bounds, recount, compact, graph_rounds=graph_rounds, keep=keep, mlp=mlp, bounds_out=bounds_out)
+    o = _opts(stream, bounds, recount, compact, graph_rounds=graph_rounds, keep=keep, mlp=mlp, bounds_out=bounds_out,
+              bucket_shift=bucket_shift)
     st = Stats()
     g = dg.c_struct()
     rc = lib().pbng_tip_decompose(ctypes.byref(g), s, int(P), out.data_ptr(), ctypes.byref(o), ctypes.byref(st))

@@ -98,7 +98,7 @@ TipParams tip_params(uint32_t P, const pbng_opts &o) {
     for (uint32_t i = 1; i < o.n_bounds; i++)
       if (o.bounds[i] <= o.bounds[i - 1]) fail(PBNG_EBOUNDS, "bounds must be strictly increasing (index %u)", i);
   }
-  TipParams p;
+  TipParams p{};
   p.P = P;
   p.bounds_mode = o.bounds_mode;
   p.bounds = o.bounds;
@@ -106,6 +106,8 @@ TipParams tip_params(uint32_t P, const pbng_opts &o) {
   p.recount = o.recount;
   p.compact = o.compact;
   p.graph_rounds = o.graph_rounds;
+  if (o.bucket_shift && (o.bucket_shift < 14 || o.bucket_shift > 30)) fail(PBNG_EINVAL, "bucket_shift must be 0 or 14..30");
+  p.bucket_shift = o.bucket_shift;
   p.timeout_ns = o.timeout_ns ? o.timeout_ns : 10000000000ull;
   p.mlp_params = o.mlp_params;
   p.mlp_hidden = o.mlp_hidden;

@@ -159,6 +159,7 @@ struct TipParams {
   const uint64_t *bounds;
   uint32_t n_bounds;
   int recount, compact, graph_rounds;
+  uint32_t bucket_shift;  // 0 = automatic
   uint64_t timeout_ns;
   const float *mlp_params;  // learned bounds (bounds_mode == PBNG_BOUNDS_LEARNED)
   uint32_t mlp_hidden, mlp_out;

@@ -21,6 +21,8 @@
 //  peels every vertex whose support equals the running minimum (ties receive
 //  the same number, exactly as one-at-a-time peeling with the clamp).
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "fdwin.cuh"
@@ -36,33 +38,42 @@ constexpr uint32_t PW_MAXW = 256, PW_CAP = 512;  // fine phase: warp-per-vertex 
 constexpr uint32_t QW_MAXW = 512, QW_CAP = 1024;  // coarse peel: warp-per-vertex shared hash
 constexpr uint32_t QG_MAXW = 2048, QG_CAP = 4096; // coarse peel: 256-thread group per vertex
 constexpr int QGT = 256;                          // threads of a group
-constexpr uint32_t PB_CAP = 8192;                // block-per-vertex shared hash slots (64 KB)
-constexpr uint32_t PB_FILL = PB_CAP / 2;         // most distinct targets a hash pass may hold
-constexpr uint32_t P_CHUNK = 2 * PB_CAP;         // block-per-vertex dense counters (same 64 KB)
+constexpr uint32_t PB_CAP = 8192;                // block-class shared hash slots (64 KB)
+constexpr uint32_t P_CHUNK = 2 * PB_CAP;         // block-class dense counters (same 64 KB)
+constexpr uint32_t BK_SHIFT_MIN = 14;            // target buckets are at least P_CHUNK ids wide
+constexpr uint64_t BOFF_BUDGET = 2ull << 30;     // most bytes of bucket offsets
+constexpr uint64_t ITEM_W = 32768;               // wedges per block-class work item (at least)
 constexpr int PB_PER_SM = 3;                     // resident blocks per SM (shared memory bound)
 constexpr uint32_t P_DENSE = 16384;              // fine phase: dense shared counters when |X_p| <= this
 constexpr int PBT = 512, PWT = 256;
 enum { PC_WARP = 0, PC_GROUP = 1, PC_BLOCK = 2, PNCLASS = 3 };
 static_assert(P_CHUNK <= 2 * PB_CAP, "dense counters share the hash table memory");
+static_assert(P_CHUNK == 1u << BK_SHIFT_MIN, "a narrow bucket fits the dense counters");
 
 using ull = unsigned long long;
 
 // ------------------------------------------------------------ peel kernels
+// Target buckets: the X ids are cut into NB buckets of 2^bshift ids, and for
+// every Y vertex boff[y][b] is the position in its current (sorted) list of
+// the first entry in bucket b, so that the slice of a list holding the
+// targets of buckets [bs, be) is two loads away.  Lists shrink by stable
+// compaction, which rewrites the offsets of the lists it touches.
 struct PeelArgs {
   const uint32_t *p_off, *p_adj;  // X -> Y
   const uint32_t *o_off, *o_adj, *o_len;  // Y -> X (current)
-  uint8_t *state;
+  const uint32_t *boff;  // ny x (nb + 1) bucket offsets, null when nb == 1
+  uint32_t nb, bshift;
   ull *sup;
-  const ull *theta_hi;
-  uint32_t *next;
-  unsigned *next_n;
   ull *updates;
   uint32_t nx;
 };
 
+// slices of the current lists being walked: start, length, and the
+// exclusive prefix of their 32-wedge chunk counts
 template <int N>
 struct PMid {
   uint32_t lo[N];
+  uint32_t len[N];
   uint32_t pre[N + 1];
 };
 
@@ -102,6 +113,55 @@ struct SubGrp {
   }
 };
 
+// support(x') -= dec.  No return value is needed (the next active set is
+// found by a scan), so this is a fire-and-forget reduction.  Targets that are
+// active or peeled may receive it too: their supports are never read again.
+__device__ __forceinline__ void sub_support(const PeelArgs &A, uint32_t xp, uint64_t dec) {
+  atomicAdd(&A.sup[xp], (ull)(0ull - dec));
+}
+
+// Wedge walk over the slices in mb (nseg of them, C chunks of 32 wedges in
+// all).  Every warp takes a contiguous run of chunks, finds the slice of its
+// first chunk by binary search and then advances slice by slice, so a chunk
+// costs a few warp instructions and its 32 list reads are coalesced; four
+// chunks are in flight per warp.
+template <int N, class F>
+__device__ __forceinline__ void walk_chunks(const PeelArgs &A, int rank, const PMid<N> &mb, int nseg, uint32_t C,
+                                            F &&f) {
+  constexpr uint32_t NW = N / 32;
+  const uint32_t lane = rank & 31, wid = rank >> 5;
+  const uint32_t per = (C + NW - 1) / NW;
+  uint32_t c = wid * per;
+  const uint32_t ce = min(C, c + per);
+  if (c >= ce) return;
+  int i = seg_of(mb.pre, nseg, c);
+  for (; c + 3 < ce; c += 4) {
+    uint32_t a[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      while (mb.pre[i + 1] <= c + u) i++;
+      uint32_t off = ((c + u - mb.pre[i]) << 5) + lane;
+      ok[u] = off < mb.len[i];
+      a[u] = mb.lo[i] + off;
+    }
+    uint32_t v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) v[u] = ok[u] ? __ldg(&A.o_adj[a[u]]) : 0u;
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      if (ok[u]) f(v[u]);
+  }
+  for (; c < ce; c++) {
+    while (mb.pre[i + 1] <= c) i++;
+    uint32_t off = ((c - mb.pre[i]) << 5) + lane;
+    if (off < mb.len[i]) f(__ldg(&A.o_adj[mb.lo[i] + off]));
+  }
+}
+
+__device__ __forceinline__ uint32_t nchunks(uint32_t len) { return (len + 31) >> 5; }
+
+// whole current lists of N(x)[base, base + N): slices into mb, returns their chunks
 template <class Grp, int N>
 __device__ __forceinline__ uint32_t peel_load(const PeelArgs &A, uint32_t xo, uint32_t xd, uint32_t base, const Grp &g,
                                               PMid<N> &mb) {
@@ -113,38 +173,23 @@ __device__ __forceinline__ uint32_t peel_load(const PeelArgs &A, uint32_t xo, ui
     len = A.o_len[y];
   }
   mb.lo[r] = lo;
-  return g.scan(len, mb.pre);
-}
-
-template <class Grp, int N, class F>
-__device__ __forceinline__ void peel_walk(const PeelArgs &A, const Grp &g, const PMid<N> &mb, uint32_t T, F &&f) {
-  for (uint32_t w = g.rank(); w < T; w += N) {
-    int i = seg_of(mb.pre, N, w);
-    f(A.o_adj[mb.lo[i] + (w - mb.pre[i])]);
-  }
-}
-
-__device__ __forceinline__ void dec_support(const PeelArgs &A, uint32_t xp, uint64_t dec, uint64_t thi) {
-  ull old = atomicAdd(&A.sup[xp], (ull)(0ull - dec));
-  if (old >= thi && old - dec < thi) {
-    unsigned p = atomicAdd(A.next_n, 1u);
-    A.next[p] = xp;
-  }
+  mb.len[r] = len;
+  return g.scan(nchunks(len), mb.pre);
 }
 
 struct PHash {
   SmemHash h;
   uint32_t cap;
   __device__ void inc(uint32_t k) const { h.inc(k); }
-  template <class Grp, int N>
-  __device__ uint64_t drain(const PeelArgs &A, uint32_t, uint32_t, const Grp &g, PMid<N> &, uint64_t thi) const {
+  template <class Grp>
+  __device__ uint64_t drain(const PeelArgs &A, const Grp &g) const {
     uint64_t nup = 0;
-    for (uint32_t i = g.rank(); i < cap; i += N) {
+    for (uint32_t i = g.rank(); i < cap; i += Grp::N) {
       uint32_t k = h.key[i];
       if (k != EMPTY_KEY) {
         uint32_t c = h.val[i];
-        if (c >= 2 && A.state[k] == ST_ALIVE) {  // active and peeled targets get nothing
-          dec_support(A, k, choose2(c), thi);
+        if (c >= 2) {
+          sub_support(A, k, choose2(c));
           nup++;
         }
         h.key[i] = EMPTY_KEY;
@@ -155,16 +200,17 @@ struct PHash {
   }
 };
 
-// returns this thread's number of support updates
+// whole vertex through one shared hash (warp and group classes); returns
+// this thread's number of support updates
 template <class Grp, int N, class Tbl>
-__device__ uint64_t peel_vertex(const PeelArgs &A, uint32_t x, const Grp &g, PMid<N> &mb, const Tbl &tbl, uint64_t thi) {
+__device__ uint64_t peel_vertex(const PeelArgs &A, uint32_t x, const Grp &g, PMid<N> &mb, const Tbl &tbl) {
   uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
   for (uint32_t base = 0; base < xd; base += N) {
-    uint32_t T = peel_load(A, xo, xd, base, g, mb);
-    peel_walk(A, g, mb, T, [&](uint32_t xp) { tbl.inc(xp); });
+    uint32_t C = peel_load(A, xo, xd, base, g, mb);
+    walk_chunks(A, g.rank(), mb, (int)min((uint32_t)N, xd - base), C, [&](uint32_t xp) { tbl.inc(xp); });
     g.sync();
   }
-  uint64_t nup = tbl.drain(A, xo, xd, g, mb, thi);
+  uint64_t nup = tbl.drain(A, g);
   g.sync();
   return nup;
 }
@@ -174,28 +220,54 @@ __device__ __forceinline__ void add_updates(const PeelArgs &A, uint64_t nup) {
   if ((threadIdx.x & 31) == 0 && nup && A.updates) atomicAdd(A.updates, (ull)nup);
 }
 
-// Slice of y's current list holding target ids in [c0, c1) (lists are sorted).
-template <int N>
-__device__ __forceinline__ uint32_t chunk_load(const PeelArgs &A, uint32_t xo, uint32_t xd, uint32_t base, uint32_t c0,
-                                               uint32_t c1, bool full, const BlockGrp<N> &g, PMid<N> &mb) {
-  int r = g.rank();
-  uint32_t lo = 0, len = 0;
-  if (base + r < xd) {
-    uint32_t y = A.p_adj[xo + base + r];
-    uint32_t s0 = A.o_off[y], L = A.o_len[y];
-    if (full) {
-      lo = s0;
-      len = L;
-    } else {
-      uint32_t a0 = lower_bound_u32(A.o_adj + s0, L, c0);
-      uint32_t a1 = a0 + lower_bound_u32(A.o_adj + s0 + a0, L - a0, c1);
-      lo = s0 + a0;
-      len = a1 - a0;
-    }
+__global__ void __launch_bounds__(PWT) k_peel_warp(PeelArgs A, const uint64_t *list, const unsigned *count) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr size_t per = align16(QW_CAP * 8 + sizeof(PMid<32>));
+  uint32_t *key = (uint32_t *)(sm + w * per), *val = key + QW_CAP;
+  PMid<32> &mb = *(PMid<32> *)(sm + w * per + QW_CAP * 8);
+  for (uint32_t i = lane; i < QW_CAP; i += 32) key[i] = EMPTY_KEY, val[i] = 0;
+  __syncwarp();
+  WarpGrp g;
+  uint64_t nup = 0;
+  unsigned n = *count;
+  for (size_t it = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; it < n; it += ((size_t)gridDim.x * blockDim.x) >> 5) {
+    uint64_t item = list[it];
+    uint32_t x = (uint32_t)item, W = (uint32_t)(item >> 32);
+    uint32_t cap = pow2_at_least(max(2u * W, 32u));
+    PHash p{SmemHash{key, val, cap - 1}, cap};
+    nup += peel_vertex(A, x, g, mb, p);
   }
-  mb.lo[r] = lo;
-  return g.scan(len, mb.pre);
+  add_updates(A, nup);
 }
+
+// two 256-thread groups per block, each with its own shared hash and named
+// barrier, one active vertex per group
+__global__ void __launch_bounds__(2 * QGT) k_peel_group(PeelArgs A, const uint64_t *list, const unsigned *count) {
+  if ((size_t)blockIdx.x * 2 >= *count) return;  // fixed grids of graph-captured rounds
+  extern __shared__ __align__(16) uint8_t sm[];
+  int sub = threadIdx.x / QGT;
+  constexpr size_t per = align16(QG_CAP * 8 + sizeof(PMid<QGT>) + (QGT / 32 + 2) * 4);
+  uint8_t *base = sm + sub * per;
+  uint32_t *key = (uint32_t *)base, *val = key + QG_CAP;
+  PMid<QGT> &mb = *(PMid<QGT> *)(base + QG_CAP * 8);
+  uint32_t *ws = (uint32_t *)(base + QG_CAP * 8 + sizeof(PMid<QGT>));
+  SubGrp<QGT> g{sub * QGT, 1 + sub, ws};
+  for (uint32_t i = g.rank(); i < QG_CAP; i += QGT) key[i] = EMPTY_KEY, val[i] = 0;
+  g.sync();
+  uint64_t nup = 0;
+  unsigned n = *count;
+  for (size_t it = (size_t)blockIdx.x * 2 + sub; it < n; it += (size_t)gridDim.x * 2) {
+    uint64_t item = list[it];
+    uint32_t x = (uint32_t)item, W = (uint32_t)(item >> 32);
+    uint32_t cap = pow2_at_least(max(2u * W, 64u));
+    PHash p{SmemHash{key, val, cap - 1}, cap};
+    nup += peel_vertex(A, x, g, mb, p);
+  }
+  add_updates(A, nup);
+}
+
+size_t peel_group_smem() { return 2 * align16(QG_CAP * 8 + sizeof(PMid<QGT>) + (QGT / 32 + 2) * 4); }
 
 // Shared hash whose keys are stored as id + 1, so that an all-zero table is
 // empty and the same memory can serve as zeroed dense counters.
@@ -218,177 +290,237 @@ struct ZHash {
   }
 };
 
-// Block per active vertex.  The target id range [0, nx) is covered by
-// consecutive ranges [c0, c1); for each range the slices of the current
-// lists holding targets in it are found by binary search (lists are sorted)
-// and its wedges are aggregated per target in 64 KB of shared memory:
-//  - dense counters when the range is at most 16K ids wide,
-//  - else an open-addressing hash when its wedges (which bound its distinct
-//    targets) fit at load 1/2; a range that would overflow is halved first.
-// The first range width is chosen from the vertex's wedge count W so that a
-// typical range fills the hash, and widths adapt to the observed density.
-// Each aggregated target x' that is still unpeeled loses C(c(x,x'), 2).
-template <int N>
-__device__ uint64_t peel_vertex_block(const PeelArgs &A, uint32_t x, uint32_t W, const BlockGrp<N> &g, PMid<N> &mb,
-                                      uint32_t *tab, uint64_t thi) {
-  uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
-  uint64_t nup = 0;
-  uint32_t width;
-  if (A.nx <= P_CHUNK || W <= PB_FILL) width = A.nx;
-  else width = (uint32_t)max((uint64_t)P_CHUNK, (uint64_t)A.nx * PB_FILL / W);
-  uint32_t c0 = 0;
-  while (c0 < A.nx) {
-    uint32_t c1 = (uint32_t)min((uint64_t)A.nx, (uint64_t)c0 + width);
-    bool full = c0 == 0 && c1 == A.nx;
-    bool dense = c1 - c0 <= P_CHUNK;
-    // wedges of the range; for xd > N only an upper bound is needed to pick
-    // the table, so sum the slice lengths chunk by chunk
-    uint32_t T = 0;
-    for (uint32_t base = 0; base < xd; base += N) T += chunk_load(A, xo, xd, base, c0, c1, full, g, mb);
-    if (T == 0) {
-      c0 = c1;
-      if (width < A.nx / 2) width *= 2;
-      continue;
-    }
-    if (!dense && T > PB_FILL) {  // too many targets for the hash: halve the range
-      width = max(P_CHUNK, (c1 - c0) / 2);
-      continue;
-    }
-    uint32_t *key = tab, *val = tab + PB_CAP;
-    uint32_t cap = dense ? 0 : pow2_at_least(max(2u * T, 64u));
-    ZHash h{key, val, cap - 1};
-    auto inc = [&](uint32_t xp) {
-      if (dense) atomicAdd(&tab[xp - c0], 1u);
-      else h.inc(xp);
-    };
-    auto take = [&](uint32_t xp) {
-      uint32_t c = atomicExch(&tab[xp - c0], 0u);
-      if (c >= 2 && A.state[xp] == ST_ALIVE) {
-        dec_support(A, xp, choose2(c), thi);
-        nup++;
-      }
-    };
-    if (xd <= (uint32_t)N) {
-      peel_walk(A, g, mb, T, inc);  // the single slice load is still in mb
-    } else {
-      for (uint32_t base = 0; base < xd; base += N) {
-        uint32_t Tb = chunk_load(A, xo, xd, base, c0, c1, full, g, mb);
-        peel_walk(A, g, mb, Tb, inc);
-        __syncthreads();
-      }
-    }
-    __syncthreads();
-    if (!dense) {  // drain the hash slot by slot
-      for (uint32_t i = g.rank(); i < cap; i += N) {
-        uint32_t k = key[i];
-        if (k) {
-          uint32_t c = val[i], xp = k - 1;
-          if (c >= 2 && A.state[xp] == ST_ALIVE) {
-            dec_support(A, xp, choose2(c), thi);
-            nup++;
-          }
-          key[i] = 0;
-          val[i] = 0;
-        }
-      }
-    } else if (T >= (c1 - c0) / 2) {  // dense and crowded: scan the counters
-      for (uint32_t i = g.rank(); i < c1 - c0; i += N) {
-        uint32_t c = tab[i];
-        if (c) {
-          tab[i] = 0;
-          uint32_t xp = c0 + i;
-          if (c >= 2 && A.state[xp] == ST_ALIVE) {
-            dec_support(A, xp, choose2(c), thi);
-            nup++;
-          }
-        }
-      }
-    } else if (xd <= (uint32_t)N) {  // dense and sparse: walk the wedges again
-      peel_walk(A, g, mb, T, take);
-    } else {
-      for (uint32_t base = 0; base < xd; base += N) {
-        uint32_t Tb = chunk_load(A, xo, xd, base, c0, c1, full, g, mb);
-        peel_walk(A, g, mb, Tb, take);
-        __syncthreads();
-      }
-    }
-    __syncthreads();
-    c0 = c1;
-    if (T < PB_FILL / 4 && width < A.nx / 2) width *= 2;
+// slice of y's current list holding the targets of buckets [bs, be)
+__device__ __forceinline__ void bucket_slice(const PeelArgs &A, uint32_t y, uint32_t bs, uint32_t be, uint32_t &lo,
+                                             uint32_t &len) {
+  uint32_t s0 = A.o_off[y];
+  if (bs == 0 && be >= A.nb) {
+    lo = s0;
+    len = A.o_len[y];
+    return;
   }
+  const uint32_t *bo = A.boff + (size_t)y * (A.nb + 1);
+  uint32_t a = bo[bs], b = bo[be];
+  lo = s0 + a;
+  len = b - a;
+}
+
+// Block-class work item: one active vertex x and a range of target buckets
+// [b0, b1) (a heavy vertex is split into several items that run on
+// different blocks; their targets are disjoint).  The block
+//  1. sums, per bucket, the wedges of x landing in it (slice lengths),
+//  2. groups consecutive buckets into passes: a bucket with more than F
+//     wedges is a pass of its own, the others are grouped by the F-multiple
+//     their prefix sum falls in, so a group holds fewer than 2F wedges,
+//  3. runs each pass: the pass's slices are walked once into 64 KB of shared
+//     memory - an open-addressing hash for a group (load at most 1/2), dense
+//     counters for a heavy bucket (a bucket wider than the dense capacity is
+//     cut into dense sub-ranges found by binary search inside its slice) -
+//     and every aggregated target x' loses C(c(x,x'), 2).
+constexpr uint32_t BK_F = PB_CAP / 4;  // F: group passes hold < 2F = PB_CAP / 2 wedges
+constexpr uint32_t NB_MAX = PBT;      // buckets per item: one per thread
+
+struct BPlan {
+  uint32_t a[NB_MAX + 1];  // per-bucket wedges, then pass starts
+  uint32_t b[NB_MAX + 1];  // flag prefix, then per-pass wedges
+};
+
+template <int N>
+__device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, uint32_t b1, const BlockGrp<N> &g,
+                                    PMid<N> &mb, BPlan &pl, uint32_t *tab) {
+  const uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo, nbi = b1 - b0;
+  const int t = threadIdx.x;
+  uint64_t nup = 0;
+  // 1. wedges per bucket
+  if (t < (int)nbi) pl.a[t] = 0;
+  __syncthreads();
+  if (nbi == 1) {
+    uint32_t s = 0;
+    for (uint32_t k = t; k < xd; k += N) {
+      uint32_t lo, len;
+      bucket_slice(A, A.p_adj[xo + k], b0, b1, lo, len);
+      s += len;
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((t & 31) == 0 && s) atomicAdd(&pl.a[0], s);
+  } else {  // warps over neighbours, lanes over buckets (one row of offsets per neighbour)
+    const uint32_t lane = t & 31, wid = t >> 5;
+    for (uint32_t j = 0; j < nbi; j += 32) {
+      uint32_t b = j + lane, s = 0;
+      if (b < nbi)
+        for (uint32_t k = wid; k < xd; k += N / 32) {
+          const uint32_t *bo = A.boff + (size_t)A.p_adj[xo + k] * (A.nb + 1) + b0 + b;
+          s += bo[1] - bo[0];
+        }
+      if (s) atomicAdd(&pl.a[b], s);
+    }
+  }
+  __syncthreads();
+  // 2. passes
+  uint32_t tb = t < (int)nbi ? pl.a[t] : 0u;
+  uint32_t tprev = (t > 0 && t < (int)nbi) ? pl.a[t - 1] : 0u;
+  g.scan(tb, mb.pre);
+  bool start = false;
+  if (t < (int)nbi)
+    start = t == 0 || tb > BK_F || tprev > BK_F || mb.pre[t] / BK_F != mb.pre[t - 1] / BK_F;
+  uint32_t np = g.scan(start ? 1u : 0u, pl.b);
+  uint32_t q = pl.b[t];
+  __syncthreads();
+  if (start) pl.a[q] = t;
+  if (t == 0) pl.a[np] = nbi;
+  __syncthreads();
+  if (t < (int)np) pl.b[t] = mb.pre[pl.a[t + 1]] - mb.pre[pl.a[t]];
+  __syncthreads();
+  // 3. passes
+  const uint32_t width = 1u << A.bshift;
+  for (uint32_t qi = 0; qi < np; qi++) {
+    const uint32_t bs = b0 + pl.a[qi], be = b0 + pl.a[qi + 1], Tq = pl.b[qi];
+    if (Tq == 0) continue;
+    const bool hash = Tq <= 2 * BK_F;
+    const uint32_t c0 = bs << A.bshift;
+    const uint32_t cend = (uint32_t)min((uint64_t)A.nx, (uint64_t)be << A.bshift);
+    // dense sub-ranges [d0, d0 + P_CHUNK) of a heavy bucket (one range unless the bucket is wider)
+    const bool narrow = hash || width <= P_CHUNK;
+    for (uint32_t d0 = c0; d0 < cend; d0 += narrow ? (cend - c0) : P_CHUNK) {
+      const uint32_t d1 = narrow ? cend : min(cend, d0 + P_CHUNK);
+      const bool dense = !hash;
+      uint32_t cap = hash ? pow2_at_least(max(2u * Tq, 64u)) : 0u;
+      ZHash h{tab, tab + PB_CAP, cap - 1};
+      auto load = [&](uint32_t base) -> uint32_t {  // slices of N(x)[base, base + N); returns chunks
+        uint32_t lo = 0, len = 0;
+        if (base + t < xd) {
+          bucket_slice(A, A.p_adj[xo + base + t], bs, be, lo, len);
+          if (!narrow) {
+            uint32_t a0 = lower_bound_u32(A.o_adj + lo, len, d0);
+            uint32_t a1 = a0 + lower_bound_u32(A.o_adj + lo + a0, len - a0, d1);
+            lo += a0;
+            len = a1 - a0;
+          }
+        }
+        mb.lo[t] = lo;
+        mb.len[t] = len;
+        return g.scan(nchunks(len), mb.pre);
+      };
+      auto inc = [&](uint32_t xp) {
+        if (dense) atomicAdd(&tab[xp - d0], 1u);
+        else h.inc(xp);
+      };
+      auto take = [&](uint32_t xp) {
+        uint32_t c = atomicExch(&tab[xp - d0], 0u);
+        if (c >= 2) {
+          sub_support(A, xp, choose2(c));
+          nup++;
+        }
+      };
+      uint32_t Cw = 0;
+      for (uint32_t base = 0; base < xd; base += N) {
+        uint32_t Cb = load(base);
+        Cw += Cb;
+        walk_chunks(A, t, mb, (int)min((uint32_t)N, xd - base), Cb, inc);
+        __syncthreads();
+      }
+      // wedges of this (sub-)range: exact from the plan, else bounded by the chunks
+      const uint64_t Tw = narrow ? (uint64_t)Tq : (uint64_t)Cw * 32;
+      if (!dense) {  // drain the hash slot by slot
+        for (uint32_t i = t; i < cap; i += N) {
+          uint32_t k = tab[i];
+          if (k) {
+            uint32_t c = tab[PB_CAP + i];
+            if (c >= 2) {
+              sub_support(A, k - 1, choose2(c));
+              nup++;
+            }
+            tab[i] = 0;
+            tab[PB_CAP + i] = 0;
+          }
+        }
+      } else if (Tw >= (d1 - d0) / 2) {  // dense and crowded: scan the counters
+        for (uint32_t i = t; i < d1 - d0; i += N) {
+          uint32_t c = tab[i];
+          if (c) {
+            tab[i] = 0;
+            if (c >= 2) {
+              sub_support(A, d0 + i, choose2(c));
+              nup++;
+            }
+          }
+        }
+      } else if (xd <= (uint32_t)N) {  // dense and sparse: walk the wedges again
+        walk_chunks(A, t, mb, (int)xd, Cw, take);
+      } else {
+        for (uint32_t base = 0; base < xd; base += N) {
+          uint32_t Cb = load(base);
+          walk_chunks(A, t, mb, (int)min((uint32_t)N, xd - base), Cb, take);
+          __syncthreads();
+        }
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();  // the plan arrays are rewritten by the next item
   return nup;
 }
 
-__global__ void __launch_bounds__(PWT) k_peel_warp(PeelArgs A, const uint64_t *list, const unsigned *count) {
-  extern __shared__ __align__(16) uint8_t sm[];
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr size_t per = align16(QW_CAP * 8 + sizeof(PMid<32>));
-  uint32_t *key = (uint32_t *)(sm + w * per), *val = key + QW_CAP;
-  PMid<32> &mb = *(PMid<32> *)(sm + w * per + QW_CAP * 8);
-  for (uint32_t i = lane; i < QW_CAP; i += 32) key[i] = EMPTY_KEY, val[i] = 0;
-  __syncwarp();
-  WarpGrp g;
-  uint64_t thi = *A.theta_hi, nup = 0;
-  unsigned n = *count;
-  for (size_t it = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; it < n; it += ((size_t)gridDim.x * blockDim.x) >> 5) {
-    uint64_t item = list[it];
-    uint32_t x = (uint32_t)item, W = (uint32_t)(item >> 32);
-    uint32_t cap = pow2_at_least(max(2u * W, 32u));
-    PHash p{SmemHash{key, val, cap - 1}, cap};
-    nup += peel_vertex(A, x, g, mb, p, thi);
-  }
-  add_updates(A, nup);
-}
-
-// two 256-thread groups per block, each with its own shared hash and named
-// barrier, one active vertex per group
-__global__ void __launch_bounds__(2 * QGT) k_peel_group(PeelArgs A, const uint64_t *list, const unsigned *count) {
-  if ((size_t)blockIdx.x * 2 >= *count) return;  // fixed grids of graph-captured rounds
-  extern __shared__ __align__(16) uint8_t sm[];
-  int sub = threadIdx.x / QGT;
-  constexpr size_t per = align16(QG_CAP * 8 + sizeof(PMid<QGT>) + (QGT / 32 + 2) * 4);
-  uint8_t *base = sm + sub * per;
-  uint32_t *key = (uint32_t *)base, *val = key + QG_CAP;
-  PMid<QGT> &mb = *(PMid<QGT> *)(base + QG_CAP * 8);
-  uint32_t *ws = (uint32_t *)(base + QG_CAP * 8 + sizeof(PMid<QGT>));
-  SubGrp<QGT> g{sub * QGT, 1 + sub, ws};
-  for (uint32_t i = g.rank(); i < QG_CAP; i += QGT) key[i] = EMPTY_KEY, val[i] = 0;
-  g.sync();
-  uint64_t thi = *A.theta_hi, nup = 0;
-  unsigned n = *count;
-  for (size_t it = (size_t)blockIdx.x * 2 + sub; it < n; it += (size_t)gridDim.x * 2) {
-    uint64_t item = list[it];
-    uint32_t x = (uint32_t)item, W = (uint32_t)(item >> 32);
-    uint32_t cap = pow2_at_least(max(2u * W, 64u));
-    PHash p{SmemHash{key, val, cap - 1}, cap};
-    nup += peel_vertex(A, x, g, mb, p, thi);
-  }
-  add_updates(A, nup);
-}
-
-size_t peel_group_smem() { return 2 * align16(QG_CAP * 8 + sizeof(PMid<QGT>) + (QGT / 32 + 2) * 4); }
-
-__global__ void __launch_bounds__(PBT) k_peel_block(PeelArgs A, const uint64_t *list, const unsigned *count) {
+__global__ void __launch_bounds__(PBT, PB_PER_SM) k_peel_block(PeelArgs A, const uint64_t *list, const unsigned *count) {
   if (blockIdx.x >= *count) return;  // fixed grids of graph-captured rounds
   extern __shared__ __align__(16) uint8_t sm[];
   PMid<PBT> &mb = *(PMid<PBT> *)sm;
   constexpr size_t o1 = align16(sizeof(PMid<PBT>));
+  constexpr size_t o2 = o1 + 256;
+  constexpr size_t o3 = o2 + align16(sizeof(BPlan));
   uint32_t *ws = (uint32_t *)(sm + o1);
   ull *ws64 = (ull *)(sm + o1 + 128);
-  uint32_t *tab = (uint32_t *)(sm + o1 + 256);  // PB_CAP keys + PB_CAP values, or P_CHUNK counters
+  BPlan &pl = *(BPlan *)(sm + o2);
+  uint32_t *tab = (uint32_t *)(sm + o3);  // PB_CAP keys + PB_CAP values, or P_CHUNK counters
   BlockGrp<PBT> g{ws, ws64};
   for (uint32_t i = threadIdx.x; i < 2 * PB_CAP; i += PBT) tab[i] = 0;  // empty hash == zero counters
   __syncthreads();
-  uint64_t thi = *A.theta_hi, nup = 0;
+  uint64_t nup = 0;
   unsigned n = *count;
   for (size_t it = blockIdx.x; it < n; it += gridDim.x) {
     uint64_t item = list[it];
-    nup += peel_vertex_block(A, (uint32_t)item, (uint32_t)(item >> 32), g, mb, tab, thi);
+    uint32_t x = (uint32_t)item, b0 = (uint32_t)(item >> 32) & 0xffffu, b1 = (uint32_t)(item >> 48);
+    nup += peel_item_block(A, x, b0, b1, g, mb, pl, tab);
   }
   add_updates(A, nup);
 }
 
-size_t peel_block_smem() { return align16(sizeof(PMid<PBT>)) + 256 + (size_t)PB_CAP * 8; }
+size_t peel_block_smem() { return align16(sizeof(PMid<PBT>)) + 256 + align16(sizeof(BPlan)) + (size_t)PB_CAP * 8; }
+
+// bucket offsets of one list (warp): bo[b] = first position whose id is in
+// bucket >= b, for b = 0..nb
+__device__ __forceinline__ void fill_boff(const uint32_t *list, uint32_t len, uint32_t *bo, uint32_t nb, uint32_t bshift,
+                                          int lane) {
+  for (uint32_t k = 0; k < len; k += 32) {
+    uint32_t p = k + lane;
+    if (p < len) {
+      uint32_t bp = list[p] >> bshift;
+      uint32_t bq = p == 0 ? 0u : (list[p - 1] >> bshift) + 1;
+      for (uint32_t b = bq; b <= bp; b++) bo[b] = p;
+    }
+  }
+  uint32_t bl = len == 0 ? 0u : (list[len - 1] >> bshift) + 1;
+  for (uint32_t b = bl + lane; b <= nb; b += 32) bo[b] = len;
+}
+
+__global__ void k_boff_build(const uint32_t *o_off, const uint32_t *o_adj, uint32_t ny, uint32_t *boff, uint32_t nb,
+                             uint32_t bshift) {
+  int lane = threadIdx.x & 31;
+  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t y = gw; y < ny; y += nw)
+    fill_boff(o_adj + o_off[y], o_off[y + 1] - o_off[y], boff + y * (size_t)(nb + 1), nb, bshift, lane);
+}
+
+// sum over Y of len^2 = the wedges of all X vertices together
+__global__ void k_sum_sq(const uint32_t *o_off, uint32_t ny, ull *out) {
+  ull s = 0;
+  for (size_t y = blockIdx.x * (size_t)blockDim.x + threadIdx.x; y < ny; y += (size_t)gridDim.x * blockDim.x) {
+    ull d = o_off[y + 1] - o_off[y];
+    s += d * d;
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
 
 // ------------------------------------------------------- round bookkeeping
 struct PrepArgs {
@@ -398,10 +530,14 @@ struct PrepArgs {
   uint32_t *part;
   uint32_t pi;
   uint8_t *state;
-  ull *sum_w;  // [0] wedges of the active set, [1] its (vertex, mid) expansions
-  uint64_t *lists;  // PNCLASS x nx
+  ull *sum_w;  // [0] wedges of the active set, [1] its (vertex, mid) expansions, [2] largest W
+  uint64_t *lists;  // warp and group classes, nx entries each: x | W << 32
+  uint64_t *blist;  // block class work items: x | b0 << 32 | b1 << 48
   unsigned *counts;
-  uint32_t nx;
+  uint32_t nx, nb;
+  uint64_t item_w;  // wedges per block-class item (at least)
+  uint8_t *lab_alive;  // re-count labels (Sec. 5.1), or null
+  const uint32_t *x2lab;
   // dynamic graph updates (Sec. 5.2): the active vertices' entries die this
   // round; a Y list is queued for compaction once a quarter of it is dead
   int compact;
@@ -434,33 +570,34 @@ __global__ void k_prep(PrepArgs A) {
     for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
     if (lane == 0) {
       A.part[x] = A.pi;
-      A.state[x] = ST_ACTIVE;  // active vertices receive no updates
+      A.state[x] = ST_ACTIVE;  // leaves the remaining graph this round
+      if (A.lab_alive) A.lab_alive[A.x2lab[x]] = 0;
       atomicAdd(&A.sum_w[0], (ull)W);
       atomicAdd(&A.sum_w[1], (ull)xd);
+      atomicMax(&A.sum_w[2], (ull)W);
       if (W >= 2) {
-        int c = W <= QW_MAXW ? PC_WARP : (W <= QG_MAXW ? PC_GROUP : PC_BLOCK);
-        unsigned p = atomicAdd(&A.counts[c], 1u);
-        A.lists[(size_t)c * A.nx + p] = (uint64_t)x | ((uint64_t)min(W, (uint64_t)0xffffffffu) << 32);
+        if (W <= QG_MAXW) {
+          int c = W <= QW_MAXW ? PC_WARP : PC_GROUP;
+          unsigned p = atomicAdd(&A.counts[c], 1u);
+          A.lists[(size_t)c * A.nx + p] = (uint64_t)x | (W << 32);
+        } else {  // K items over equal shares of the target buckets
+          uint32_t K = (uint32_t)min((uint64_t)A.nb, (W + A.item_w - 1) / A.item_w);
+          unsigned p = atomicAdd(&A.counts[PC_BLOCK], K);
+          for (uint32_t k = 0; k < K; k++) {
+            uint64_t b0 = (uint64_t)k * A.nb / K, b1 = (uint64_t)(k + 1) * A.nb / K;
+            A.blist[p + k] = (uint64_t)x | (b0 << 32) | (b1 << 48);
+          }
+        }
       }
     }
   }
 }
 
-__global__ void k_mark_peeled(const uint32_t *f, uint32_t nf, uint8_t *state, uint8_t *lab_alive, const uint32_t *x2lab,
-                              const unsigned *nf_dev = nullptr) {
-  if (nf_dev) nf = *nf_dev;
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < nf; j += (size_t)gridDim.x * blockDim.x) {
-    uint32_t x = f[j];
-    state[x] = ST_PEELED;
-    if (lab_alive) lab_alive[x2lab[x]] = 0;
-  }
-}
-
 // device-resident state of the graph-captured coarse rounds
 struct RoundDev {
-  unsigned nf, nn, touched_n, pi;
+  unsigned nf, nn, touched_n, pi, na, pad_;
   unsigned counts[4];
-  ull sum_w[2];
+  ull sum_w[3];
   ull tot_wedges, tot_exp, tot_front, rounds, part_work, iters;
 };
 
@@ -468,7 +605,7 @@ __global__ void k_round_reset(RoundDev *R) {
   R->nn = 0;
   R->touched_n = 0;
   for (int i = 0; i < 4; i++) R->counts[i] = 0;
-  R->sum_w[0] = R->sum_w[1] = 0;
+  R->sum_w[0] = R->sum_w[1] = R->sum_w[2] = 0;
 }
 
 // end of one round: totals, next frontier size, and (last round of the body)
@@ -490,7 +627,8 @@ __global__ void k_round_end(RoundDev *R, cudaGraphConditionalHandle h, int set_c
 
 // warp per touched Y vertex: stable in-place removal of peeled X entries
 __global__ void k_compact(const uint32_t *touched, const unsigned *tn, const uint32_t *o_off, uint32_t *o_adj, uint32_t *o_len,
-                          uint32_t *ytouch, uint32_t *dead, const uint8_t *state) {
+                          uint32_t *ytouch, uint32_t *dead, const uint8_t *state, uint32_t *boff, uint32_t nb,
+                          uint32_t bshift) {
   int lane = threadIdx.x & 31;
   size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
   unsigned n = *tn;
@@ -509,6 +647,10 @@ __global__ void k_compact(const uint32_t *touched, const unsigned *tn, const uin
       if (keep) o_adj[lo + out + __popc(b & ((1u << lane) - 1u))] = x;
       out += __popc(b);
       __syncwarp();
+    }
+    if (boff) {  // the list's bucket offsets
+      __syncwarp();
+      fill_boff(o_adj + lo, out, boff + (size_t)y * (nb + 1), nb, bshift, lane);
     }
     if (lane == 0) {
       o_len[y] = out;
@@ -582,18 +724,35 @@ __global__ void k_weights(const uint32_t *alist, uint32_t na, const uint32_t *p_
 
 // start of a range (snapshot = 1): init <- support; any pass: the active set
 // is every unpeeled vertex with support below theta_hi
+// Next active set: every remaining vertex still alive with support below the
+// range's upper bound (also the first active set of a range, with the
+// snapshot of the supports into init).
 __global__ void k_scan_frontier(const uint32_t *alist, uint32_t na, uint8_t *state, const ull *sup, ull *init,
-                                const ull *theta_hi, int snapshot, uint32_t *f, unsigned *fn) {
+                                const ull *theta_hi, int snapshot, uint32_t *f, unsigned *fn,
+                                const unsigned *na_dev = nullptr) {
   ull thi = *theta_hi;
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < na; j += (size_t)gridDim.x * blockDim.x) {
-    uint32_t x = alist[j];
-    if (state[x] != ST_ALIVE) continue;
-    ull s = sup[x];
-    if (snapshot) init[x] = s;
-    if (s < thi) {
+  if (na_dev) na = *na_dev;
+  int lane = threadIdx.x & 31;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t j0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) & ~(size_t)31; j0 < na; j0 += stride) {
+    size_t j = j0 + lane;
+    bool take = false;
+    uint32_t x = 0;
+    if (j < na) {
+      x = alist[j];
+      if (state[x] == ST_ALIVE) {
+        ull s = sup[x];
+        if (snapshot) init[x] = s;
+        take = s < thi;
+      }
+    }
+    unsigned b = __ballot_sync(0xffffffffu, take);
+    unsigned base = 0;
+    if (lane == 0 && b) base = atomicAdd(fn, (unsigned)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take) {
       state[x] = ST_ACTIVE;
-      unsigned p = atomicAdd(fn, 1u);
-      f[p] = x;
+      f[base + __popc(b & ((1u << lane) - 1u))] = x;
     }
   }
 }
@@ -950,10 +1109,53 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   CK_LAUNCH();
   uint32_t *ytouch = a.zeros<uint32_t>(ny + 1), *touched = a.alloc<uint32_t>(ny + 1), *dead = a.zeros<uint32_t>(ny + 1);
   uint32_t *front = a.alloc<uint32_t>(nx), *front2 = a.alloc<uint32_t>(nx);
-  uint64_t *plists = a.alloc<uint64_t>((size_t)PNCLASS * nx);
+  uint64_t *plists = a.alloc<uint64_t>((size_t)2 * nx);
+  // target buckets and their offsets in every Y list
+  uint32_t bshift = std::max(BK_SHIFT_MIN, prm.bucket_shift);
+  while (bshift < 31 && (((uint64_t)nx + (1ull << bshift) - 1) >> bshift > NB_MAX ||
+                         (uint64_t)ny * ((((uint64_t)nx + (1ull << bshift) - 1) >> bshift) + 1) * 4 > BOFF_BUDGET))
+    bshift++;
+  const uint32_t nb = (uint32_t)(((uint64_t)nx + (1ull << bshift) - 1) >> bshift);
+  uint32_t *boff = nullptr;
+  if (nb > 1) {
+    boff = a.alloc<uint32_t>((size_t)ny * (nb + 1));
+    k_boff_build<<<grid_for((size_t)ny * 32, T, 8 * cap), T, 0, a.st>>>(o_off, o_adj, ny, boff, nb, bshift);
+    CK_LAUNCH();
+  }
+  // block-class items: at most one per active vertex plus one per item_w of
+  // its wedges; the wedges of all X vertices together bound a round's
+  uint64_t item_w = ITEM_W, wtot = 0;
+  {
+    ull *d = a.zeros<ull>(1);
+    k_sum_sq<<<grid_for(ny, T, cap), T, 0, a.st>>>(o_off, ny, d);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(&wtot, d, 8, cudaMemcpyDeviceToHost, a.st));
+    CK(cudaStreamSynchronize(a.st));
+    a.free(d);
+  }
+  item_w = std::max<uint64_t>(item_w, wtot / (4ull * nx) + 1);
+  const uint64_t bcap = (uint64_t)nx + wtot / item_w + 1;
+  uint64_t *blist = a.alloc<uint64_t>(bcap);
   // small device counters: [0] frontier size, [1] next size, [2] touched, [3..6] class counts, [7] alist size
   unsigned *dc = a.zeros<unsigned>(16);
-  ull *sumw = a.zeros<ull>(2);
+  ull *sumw = a.zeros<ull>(4);
+  // per-round trace (env PBNG_TRACE=<file>): one line per coarse round
+  struct Trace {
+    FILE *f = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    ~Trace() {
+      if (f) fclose(f);
+      for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    }
+  } tr;
+  if (const char *tp = getenv("PBNG_TRACE")) {
+    tr.f = fopen(tp, "a");
+    if (tr.f)
+      for (auto &e : tr.ev) CK(cudaEventCreate(&e));
+  }
+  FILE *trace = tr.f;
+  cudaEvent_t *tev = tr.ev;
   uint64_t exp_cd = 0, front_cd = 0;
   RangeState *rs = a.zeros<RangeState>(1);
   ull *wl = a.alloc<ull>(nx);
@@ -964,9 +1166,10 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   PA.o_off = o_off;
   PA.o_adj = o_adj;
   PA.o_len = o_len;
-  PA.state = state;
+  PA.boff = boff;
+  PA.nb = nb;
+  PA.bshift = bshift;
   PA.sup = sup;
-  PA.theta_hi = &rs->theta_hi;
   PA.updates = dwedge + 8;
   PA.nx = nx;
 
@@ -993,6 +1196,32 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       if (g) cudaGraphDestroy(g);
     }
   } gh;
+  auto prep_args = [&](const uint32_t *F, uint32_t nf, uint32_t pi, ull *sum_w, unsigned *counts, unsigned *touched_n) {
+    PrepArgs R{};
+    R.frontier = F;
+    R.nf = nf;
+    R.p_off = p_off;
+    R.p_adj = p_adj;
+    R.o_len = o_len;
+    R.part = part;
+    R.pi = pi;
+    R.state = state;
+    R.sum_w = sum_w;
+    R.lists = plists;
+    R.blist = blist;
+    R.counts = counts;
+    R.nx = nx;
+    R.nb = nb;
+    R.item_w = item_w;
+    R.lab_alive = lab_alive;
+    R.x2lab = x2lab;
+    R.compact = prm.compact;
+    R.dead = dead;
+    R.ytouch = ytouch;
+    R.touched = touched;
+    R.touched_n = touched_n;
+    return R;
+  };
   bool use_graph = prm.graph_rounds != 0;
   RoundDev *Rd = use_graph ? a.zeros<RoundDev>(1) : nullptr;
   auto build_round_graph = [&]() {
@@ -1014,35 +1243,16 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     for (int half = 0; half < 2; half++) {
       uint32_t *F = half == 0 ? front : front2, *Nx = half == 0 ? front2 : front;
       k_round_reset<<<1, 1, 0, cs>>>(Rd);
-      PrepArgs R{};
-      R.frontier = F;
-      R.nf = 0;
-      R.p_off = p_off;
-      R.p_adj = p_adj;
-      R.o_len = o_len;
-      R.part = part;
-      R.pi = 0;
-      R.state = state;
-      R.sum_w = Rd->sum_w;
-      R.lists = plists;
-      R.counts = Rd->counts;
-      R.nx = nx;
-      R.compact = prm.compact;
-      R.dead = dead;
-      R.ytouch = ytouch;
-      R.touched = touched;
-      R.touched_n = &Rd->touched_n;
+      PrepArgs R = prep_args(F, 0, 0, Rd->sum_w, Rd->counts, &Rd->touched_n);
       R.nf_dev = &Rd->nf;
       R.pi_dev = &Rd->pi;
       k_prep<<<16 * sms, T, 0, cs>>>(R);
-      PeelArgs P2 = PA;
-      P2.next = Nx;
-      P2.next_n = &Rd->nn;
-      k_peel_warp<<<6 * sms, PWT, wsm, cs>>>(P2, plists + (size_t)PC_WARP * nx, Rd->counts + PC_WARP);
-      k_peel_group<<<3 * sms, 2 * QGT, peel_group_smem(), cs>>>(P2, plists + (size_t)PC_GROUP * nx, Rd->counts + PC_GROUP);
-      k_peel_block<<<PB_PER_SM * sms, PBT, peel_block_smem(), cs>>>(P2, plists + (size_t)PC_BLOCK * nx, Rd->counts + PC_BLOCK);
-      k_mark_peeled<<<8 * sms, T, 0, cs>>>(F, 0, state, lab_alive, x2lab, &Rd->nf);
-      if (prm.compact) k_compact<<<4 * sms, T, 0, cs>>>(touched, &Rd->touched_n, o_off, o_adj, o_len, ytouch, dead, state);
+      k_peel_warp<<<6 * sms, PWT, wsm, cs>>>(PA, plists + (size_t)PC_WARP * nx, Rd->counts + PC_WARP);
+      k_peel_group<<<3 * sms, 2 * QGT, peel_group_smem(), cs>>>(PA, plists + (size_t)PC_GROUP * nx, Rd->counts + PC_GROUP);
+      k_peel_block<<<PB_PER_SM * sms, PBT, peel_block_smem(), cs>>>(PA, blist, Rd->counts + PC_BLOCK);
+      if (prm.compact)
+        k_compact<<<4 * sms, T, 0, cs>>>(touched, &Rd->touched_n, o_off, o_adj, o_len, ytouch, dead, state, boff, nb, bshift);
+      k_scan_frontier<<<cap, T, 0, cs>>>(alist, 0, state, sup, init, &rs->theta_hi, 0, Nx, &Rd->nn, &Rd->na);
       k_round_end<<<1, 1, 0, cs>>>(Rd, h, half == 1);
     }
     cudaGraph_t captured = nullptr;
@@ -1081,7 +1291,10 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       k_compact_list<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, alist2, dc + 7);
       CK_LAUNCH();
       na = fetch(a, dc + 7);
-      std::swap(alist, alist2);
+      if (use_graph)  // the captured rounds read the remaining list at a fixed address
+        CK(cudaMemcpyAsync(alist, alist2, (size_t)na * 4, cudaMemcpyDeviceToDevice, a.st));
+      else
+        std::swap(alist, alist2);
       if (na == 0) break;
     }
     // ---- range [theta(i), theta(i+1)) (Alg. 4 l.8, Sec. 3.1.3)
@@ -1148,6 +1361,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       CK(cudaMemsetAsync(&Rd->nf, 0, 8, a.st));  // nf, nn
       CK(cudaMemsetAsync(&Rd->part_work, 0, 8, a.st));
       CK(cudaMemcpyAsync(&Rd->pi, &pi, 4, cudaMemcpyHostToDevice, a.st));
+      CK(cudaMemcpyAsync(&Rd->na, &na, 4, cudaMemcpyHostToDevice, a.st));
       k_scan_frontier<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, sup, init, &rs->theta_hi, 1, front, &Rd->nf);
       CK_LAUNCH();
       if (!gh.e) build_round_graph();
@@ -1175,31 +1389,14 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     while (nf > 0) {
       rounds++;
       CK(cudaMemsetAsync(dc + 1, 0, 6 * 4, a.st));
-      CK(cudaMemsetAsync(sumw, 0, 16, a.st));
-      PrepArgs R{};
-      R.frontier = front;
-      R.nf = nf;
-      R.p_off = p_off;
-      R.p_adj = p_adj;
-      R.o_len = o_len;
-      R.part = part;
-      R.pi = pi;
-      R.state = state;
-      R.sum_w = sumw;
-      R.lists = plists;
-      R.counts = dc + 3;
-      R.nx = nx;
-      R.compact = prm.compact;
-      R.dead = dead;
-      R.ytouch = ytouch;
-      R.touched = touched;
-      R.touched_n = dc + 2;
+      CK(cudaMemsetAsync(sumw, 0, 24, a.st));
+      PrepArgs R = prep_args(front, nf, pi, sumw, dc + 3, dc + 2);
       k_prep<<<grid_for((size_t)nf * 32, T, cap), T, 0, a.st>>>(R);
       CK_LAUNCH();
       unsigned hc[6];
-      ull hw2[2];
+      ull hw2[3];
       CK(cudaMemcpyAsync(hc, dc + 1, sizeof(hc), cudaMemcpyDeviceToHost, a.st));
-      CK(cudaMemcpyAsync(hw2, sumw, 16, cudaMemcpyDeviceToHost, a.st));
+      CK(cudaMemcpyAsync(hw2, sumw, 24, cudaMemcpyDeviceToHost, a.st));
       CK(cudaStreamSynchronize(a.st));
       ull hw = hw2[0];
       cur_final += hw;
@@ -1207,8 +1404,6 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       if (do_recount) {
         // Sec. 5.1: re-count the remaining vertices instead of peeling
         recounts++;
-        k_mark_peeled<<<grid_for(nf, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab);
-        CK_LAUNCH();
         CK(cudaMemsetAsync(cnt_lab, 0, (size_t)G.n * 8, a.st));
         CountOut rc;
         rc.cnt_lab = (uint64_t *)cnt_lab;
@@ -1223,9 +1418,8 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
         wedges_cd += hw;
         exp_cd += hw2[1];
         front_cd += nf;
-        PA.next = front2;
+        if (trace) CK(cudaEventRecord(tev[0], a.st));
         g_prof.begin(PROF_PEEL);
-        PA.next_n = dc + 1;
         if (hc[2 + PC_WARP]) {
           k_peel_warp<<<grid_for((size_t)hc[2 + PC_WARP] * 32, PWT, 6 * sms), PWT, wsm, a.st>>>(PA, plists + (size_t)PC_WARP * nx,
                                                                                                 dc + 3 + PC_WARP);
@@ -1238,23 +1432,27 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
         }
         if (hc[2 + PC_BLOCK]) {
           k_peel_block<<<std::min<unsigned>(hc[2 + PC_BLOCK], PB_PER_SM * sms), PBT, peel_block_smem(), a.st>>>(
-              PA, plists + (size_t)PC_BLOCK * nx, dc + 3 + PC_BLOCK);
+              PA, blist, dc + 3 + PC_BLOCK);
           CK_LAUNCH();
         }
         g_prof.end();
-        k_mark_peeled<<<grid_for(nf, T, cap), T, 0, a.st>>>(front, nf, state, lab_alive, x2lab);
-        CK_LAUNCH();
+        if (trace) CK(cudaEventRecord(tev[1], a.st));
       }
       if (prm.compact) {
-        k_compact<<<4 * sms, T, 0, a.st>>>(touched, dc + 2, o_off, o_adj, o_len, ytouch, dead, state);
+        k_compact<<<4 * sms, T, 0, a.st>>>(touched, dc + 2, o_off, o_adj, o_len, ytouch, dead, state, boff, nb, bshift);
         CK_LAUNCH();
       }
-      if (do_recount) {
-        CK(cudaMemsetAsync(dc + 1, 0, 4, a.st));
-        k_scan_frontier<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, sup, init, &rs->theta_hi, 0, front2, dc + 1);
-        CK_LAUNCH();
+      // next active set (dc[1] was cleared with the class counters)
+      k_scan_frontier<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, sup, init, &rs->theta_hi, 0, front2, dc + 1);
+      CK_LAUNCH();
+      uint32_t nf_next = fetch(a, dc + 1);
+      if (trace) {
+        float ms = 0.f;
+        if (!do_recount) CK(cudaEventElapsedTime(&ms, tev[0], tev[1]));
+        fprintf(trace, "%d %u %llu %u %u %u %u %llu %llu %d %.4f\n", side, pi, (unsigned long long)rounds, nf,
+                hc[2 + PC_WARP], hc[2 + PC_GROUP], hc[2 + PC_BLOCK], hw, hw2[2], (int)do_recount, ms);
       }
-      nf = fetch(a, dc + 1);
+      nf = nf_next;
       std::swap(front, front2);
     }
     pi++;

@@ -127,6 +127,30 @@ def test_tip_graph_rounds_same_work_as_host_loop(pbng, compact):
             assert sa[k] == sb[k], k
 
 
+_BK_GRAPH = {}
+
+
+def bucket_graph():
+    """80k x 4k Chung-Lu graph: the peeled side spans several target buckets."""
+    if not _BK_GRAPH:
+        g = gen.chung_lu(80000, 4000, 300000, 2.3, 2.3, 2000, seed=77)
+        _BK_GRAPH["g"], _BK_GRAPH["U"] = g, oracle.tip(g, "U")
+    return _BK_GRAPH["g"], _BK_GRAPH["U"]
+
+
+@pytest.mark.parametrize("shift", [0, 15, 16, 17])
+@pytest.mark.parametrize("graph_rounds", [False, True])
+def test_tip_bucket_widths(pbng, shift, graph_rounds):
+    """Target buckets of 2^14 ids (dense passes), and wider buckets whose heavy
+    passes are cut into dense sub-ranges, with and without compaction."""
+    g, want = bucket_graph()
+    dg = pbng.to_device(g)
+    for compact in (True, False):
+        got = pbng.as_u64(pbng.tip_decompose(dg, "U", P=30, bucket_shift=shift, compact=compact,
+                                             graph_rounds=graph_rounds))
+        assert np.array_equal(got, want)
+
+
 def test_tip_explicit_and_random_bounds(pbng):
     name = "chunglu_20k_4k_200k"
     g = GRAPHS[name]
