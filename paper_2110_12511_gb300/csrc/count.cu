@@ -50,7 +50,8 @@ template <int N>
 struct MidBuf {
   uint32_t mid[N];
   uint32_t lo[N];
-  uint32_t pre[N + 1];
+  uint32_t len[N];
+  uint32_t pre[N + 1];  // exclusive prefix of the slices' 32-entry chunk counts
   unsigned long long acc[N];
 };
 
@@ -70,16 +71,15 @@ __device__ __forceinline__ uint32_t load_mids(const CArgs &A, uint32_t s, uint32
   }
   mb.mid[r] = mid;
   mb.lo[r] = lo;
-  return g.scan(len, mb.pre);
+  mb.len[r] = len;
+  return g.scan(nchunks(len), mb.pre);  // chunks
 }
 
+// the wedges of the mids in mb (C chunks, mids [base, base + N) of sd)
 template <class Grp, int N, class F>
-__device__ __forceinline__ void walk(const CArgs &A, const Grp &g, const MidBuf<N> &mb, uint32_t T, F &&f) {
-  for (uint32_t w = g.rank(); w < T; w += N) {
-    int i = seg_of(mb.pre, N, w);
-    uint32_t pos = mb.lo[i] + (w - mb.pre[i]);
-    f(i, pos, A.adj[pos]);
-  }
+__device__ __forceinline__ void walk(const CArgs &A, const Grp &g, const MidBuf<N> &mb, uint32_t sd, uint32_t base,
+                                     uint32_t C, F &&f) {
+  walk_chunks<N>(A.adj, g.rank(), mb.lo, mb.len, mb.pre, (int)min((uint32_t)N, sd - base), C, f);
 }
 
 // Table policies --------------------------------------------------------
@@ -145,8 +145,8 @@ struct GlobalPolicy {  // per-block dense counters over all labels in global mem
                             MidBuf<N> &mb, uint64_t &nat, uint64_t &nb, uint64_t &np) const {
     uint64_t ss = 0;
     for (uint32_t base = 0; base < sd; base += N) {
-      uint32_t T = load_mids(A, s, so, sd, base, g, mb);
-      walk(A, g, mb, T, [&](int, uint32_t, uint32_t last) {
+      uint32_t C = load_mids(A, s, so, sd, base, g, mb);
+      walk(A, g, mb, sd, base, C, [&](int, uint32_t, uint32_t last) {
         if (A.alive && !A.alive[last]) return;
         uint32_t x = atomicExch(&c[last], 0u);  // first visitor of last takes its count
         if (x >= 2) {
@@ -171,8 +171,8 @@ __device__ void count_start(const CArgs &A, uint32_t s, const Grp &g, MidBuf<N> 
   uint64_t wc = 0, nat = 0;
   // pass 1: wedge_count[last]++ for every valid wedge (Alg. 1 l.9-13)
   for (uint32_t base = 0; base < sd; base += N) {
-    uint32_t T = load_mids(A, s, so, sd, base, g, mb);
-    walk(A, g, mb, T, [&](int, uint32_t, uint32_t last) {
+    uint32_t C = load_mids(A, s, so, sd, base, g, mb);
+    walk(A, g, mb, sd, base, C, [&](int, uint32_t, uint32_t last) {
       if (A.alive && !A.alive[last]) return;
       tbl.inc(last);
       wc++;
@@ -183,8 +183,8 @@ __device__ void count_start(const CArgs &A, uint32_t s, const Grp &g, MidBuf<N> 
   // (Alg. 1 l.18-19 and l.21-23)
   if (md || A.cnt_e) {
     for (uint32_t base = 0; base < sd; base += N) {
-      uint32_t T = load_mids(A, s, so, sd, base, g, mb);
-      walk(A, g, mb, T, [&](int i, uint32_t pos, uint32_t last) {
+      uint32_t C = load_mids(A, s, so, sd, base, g, mb);
+      walk(A, g, mb, sd, base, C, [&](int i, uint32_t pos, uint32_t last) {
         if (A.alive && !A.alive[last]) return;
         uint32_t c = tbl.get(last);
         if (c >= 2) {

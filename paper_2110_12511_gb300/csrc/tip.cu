@@ -120,46 +120,12 @@ __device__ __forceinline__ void sub_support(const PeelArgs &A, uint32_t xp, uint
   atomicAdd(&A.sup[xp], (ull)(0ull - dec));
 }
 
-// Wedge walk over the slices in mb (nseg of them, C chunks of 32 wedges in
-// all).  Every warp takes a contiguous run of chunks, finds the slice of its
-// first chunk by binary search and then advances slice by slice, so a chunk
-// costs a few warp instructions and its 32 list reads are coalesced; four
-// chunks are in flight per warp.
+// wedge walk over the slices in mb (see walk_chunks in wedge.cuh); f(x')
 template <int N, class F>
-__device__ __forceinline__ void walk_chunks(const PeelArgs &A, int rank, const PMid<N> &mb, int nseg, uint32_t C,
+__device__ __forceinline__ void walk_slices(const PeelArgs &A, int rank, const PMid<N> &mb, int nseg, uint32_t C,
                                             F &&f) {
-  constexpr uint32_t NW = N / 32;
-  const uint32_t lane = rank & 31, wid = rank >> 5;
-  const uint32_t per = (C + NW - 1) / NW;
-  uint32_t c = wid * per;
-  const uint32_t ce = min(C, c + per);
-  if (c >= ce) return;
-  int i = seg_of(mb.pre, nseg, c);
-  for (; c + 3 < ce; c += 4) {
-    uint32_t a[4];
-    bool ok[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      while (mb.pre[i + 1] <= c + u) i++;
-      uint32_t off = ((c + u - mb.pre[i]) << 5) + lane;
-      ok[u] = off < mb.len[i];
-      a[u] = mb.lo[i] + off;
-    }
-    uint32_t v[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) v[u] = ok[u] ? __ldg(&A.o_adj[a[u]]) : 0u;
-#pragma unroll
-    for (int u = 0; u < 4; u++)
-      if (ok[u]) f(v[u]);
-  }
-  for (; c < ce; c++) {
-    while (mb.pre[i + 1] <= c) i++;
-    uint32_t off = ((c - mb.pre[i]) << 5) + lane;
-    if (off < mb.len[i]) f(__ldg(&A.o_adj[mb.lo[i] + off]));
-  }
+  walk_chunks<N>(A.o_adj, rank, mb.lo, mb.len, mb.pre, nseg, C, [&](int, uint32_t, uint32_t v) { f(v); });
 }
-
-__device__ __forceinline__ uint32_t nchunks(uint32_t len) { return (len + 31) >> 5; }
 
 // whole current lists of N(x)[base, base + N): slices into mb, returns their chunks
 template <class Grp, int N>
@@ -207,7 +173,7 @@ __device__ uint64_t peel_vertex(const PeelArgs &A, uint32_t x, const Grp &g, PMi
   uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
   for (uint32_t base = 0; base < xd; base += N) {
     uint32_t C = peel_load(A, xo, xd, base, g, mb);
-    walk_chunks(A, g.rank(), mb, (int)min((uint32_t)N, xd - base), C, [&](uint32_t xp) { tbl.inc(xp); });
+    walk_slices(A, g.rank(), mb, (int)min((uint32_t)N, xd - base), C, [&](uint32_t xp) { tbl.inc(xp); });
     g.sync();
   }
   uint64_t nup = tbl.drain(A, g);
@@ -309,21 +275,51 @@ __device__ __forceinline__ void bucket_slice(const PeelArgs &A, uint32_t y, uint
 // [b0, b1) (a heavy vertex is split into several items that run on
 // different blocks; their targets are disjoint).  The block
 //  1. sums, per bucket, the wedges of x landing in it (slice lengths),
-//  2. groups consecutive buckets into passes: a bucket with more than F
-//     wedges is a pass of its own, the others are grouped by the F-multiple
-//     their prefix sum falls in, so a group holds fewer than 2F wedges,
-//  3. runs each pass: the pass's slices are walked once into 64 KB of shared
-//     memory - an open-addressing hash for a group (load at most 1/2), dense
-//     counters for a heavy bucket (a bucket wider than the dense capacity is
-//     cut into dense sub-ranges found by binary search inside its slice) -
-//     and every aggregated target x' loses C(c(x,x'), 2).
-constexpr uint32_t BK_F = PB_CAP / 4;  // F: group passes hold < 2F = PB_CAP / 2 wedges
+//  2. cuts the buckets greedily into passes: a bucket with more than G
+//     wedges starts a dense pass (16-bit counters over 32K ids when x has
+//     fewer than 2^16 neighbours, else 32-bit counters over 16K ids), the
+//     others are grouped while their wedges stay within G,
+//  3. runs each pass: its slices are walked once into 64 KB of shared memory
+//     - an open-addressing hash for a group (load at most 1/2), dense
+//     counters for a heavy range (a bucket wider than the counters is cut
+//     into sub-ranges found by binary search inside its slices) - and every
+//     aggregated target x' loses C(c(x,x'), 2).
+constexpr uint32_t BK_G = PB_CAP / 2;  // most wedges (hence targets) of a hash pass
 constexpr uint32_t NB_MAX = PBT;      // buckets per item: one per thread
 
 struct BPlan {
   uint32_t a[NB_MAX + 1];  // per-bucket wedges, then pass starts
-  uint32_t b[NB_MAX + 1];  // flag prefix, then per-pass wedges
+  uint32_t b[NB_MAX + 1];  // prefix of the wedges, then per-pass wedges
+  uint32_t np;
 };
+
+// drain of dense counters (16-bit pairs or 32-bit) over ids [d0, d0 + n):
+// 16-byte vector reads, zeroed where touched
+template <bool W16>
+__device__ __forceinline__ uint64_t drain_dense(const PeelArgs &A, uint32_t *tab, uint32_t d0, uint32_t n, int t, int N) {
+  constexpr uint32_t PER = W16 ? 8 : 4;  // counters per 16 bytes
+  uint64_t nup = 0;
+  uint4 *v = (uint4 *)tab;
+  for (uint32_t i = t; i * PER < n; i += N) {
+    uint4 q = v[i];
+    if ((q.x | q.y | q.z | q.w) == 0u) continue;
+    v[i] = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (!w[k]) continue;
+      if (W16) {
+        uint32_t lo = w[k] & 0xffffu, hi = w[k] >> 16, id = d0 + i * PER + 2 * k;
+        if (lo >= 2) sub_support(A, id, choose2(lo)), nup++;
+        if (hi >= 2) sub_support(A, id + 1, choose2(hi)), nup++;
+      } else if (w[k] >= 2) {
+        sub_support(A, d0 + i * PER + k, choose2(w[k]));
+        nup++;
+      }
+    }
+  }
+  return nup;
+}
 
 template <int N>
 __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, uint32_t b1, const BlockGrp<N> &g,
@@ -331,15 +327,29 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
   const uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo, nbi = b1 - b0;
   const int t = threadIdx.x;
   uint64_t nup = 0;
+  // this thread's neighbour (items of vertices with at most N neighbours)
+  const bool cached = xd <= (uint32_t)N;
+  uint32_t my_s0 = 0, my_len = 0;
+  const uint32_t *my_bo = nullptr;
+  if (cached && t < (int)xd) {
+    uint32_t y = A.p_adj[xo + t];
+    my_s0 = A.o_off[y];
+    my_len = A.o_len[y];
+    if (A.boff) my_bo = A.boff + (size_t)y * (A.nb + 1);
+  }
   // 1. wedges per bucket
   if (t < (int)nbi) pl.a[t] = 0;
   __syncthreads();
   if (nbi == 1) {
     uint32_t s = 0;
-    for (uint32_t k = t; k < xd; k += N) {
-      uint32_t lo, len;
-      bucket_slice(A, A.p_adj[xo + k], b0, b1, lo, len);
-      s += len;
+    if (cached) {
+      if (t < (int)xd) s = my_bo ? my_bo[b1] - my_bo[b0] : my_len;
+    } else {
+      for (uint32_t k = t; k < xd; k += N) {
+        uint32_t lo, len;
+        bucket_slice(A, A.p_adj[xo + k], b0, b1, lo, len);
+        s += len;
+      }
     }
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((t & 31) == 0 && s) atomicAdd(&pl.a[0], s);
@@ -356,102 +366,120 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
     }
   }
   __syncthreads();
-  // 2. passes
-  uint32_t tb = t < (int)nbi ? pl.a[t] : 0u;
-  uint32_t tprev = (t > 0 && t < (int)nbi) ? pl.a[t - 1] : 0u;
-  g.scan(tb, mb.pre);
-  bool start = false;
-  if (t < (int)nbi)
-    start = t == 0 || tb > BK_F || tprev > BK_F || mb.pre[t] / BK_F != mb.pre[t - 1] / BK_F;
-  uint32_t np = g.scan(start ? 1u : 0u, pl.b);
-  uint32_t q = pl.b[t];
-  __syncthreads();
-  if (start) pl.a[q] = t;
-  if (t == 0) pl.a[np] = nbi;
-  __syncthreads();
-  if (t < (int)np) pl.b[t] = mb.pre[pl.a[t + 1]] - mb.pre[pl.a[t]];
-  __syncthreads();
-  // 3. passes
+  // 2. passes (greedy, one thread; pass starts into a, pass wedges into b)
+  g.scan(t < (int)nbi ? pl.a[t] : 0u, pl.b);
+  const bool w16 = xd < 65536u;  // a count never exceeds the number of neighbours
+  const uint32_t dcap = w16 ? 2 * P_CHUNK : P_CHUNK;  // ids of one dense pass
   const uint32_t width = 1u << A.bshift;
+  const uint32_t dspan = width <= dcap ? dcap >> A.bshift : 1u;
+  if (t == 0) {
+    uint32_t s = 0, q = 0;
+    while (s < nbi) {
+      uint32_t e;
+      if (pl.b[s + 1] - pl.b[s] > BK_G) {
+        e = min(nbi, s + dspan);
+      } else {  // largest e with wedges(s..e) <= G
+        uint32_t lo = s + 1, hi = nbi, lim = pl.b[s] + BK_G;
+        while (lo < hi) {
+          uint32_t mid = (lo + hi + 1) >> 1;
+          if (pl.b[mid] <= lim) lo = mid;
+          else hi = mid - 1;
+        }
+        e = lo;
+      }
+      uint32_t T = pl.b[e] - pl.b[s];
+      pl.a[q] = s;
+      pl.b[q] = T;  // q <= s: no later read of the prefix looks at or below q
+      q++;
+      s = e;
+    }
+    pl.a[q] = nbi;
+    pl.np = q;
+  }
+  __syncthreads();
+  const uint32_t np = pl.np;
+  // 3. passes
   for (uint32_t qi = 0; qi < np; qi++) {
     const uint32_t bs = b0 + pl.a[qi], be = b0 + pl.a[qi + 1], Tq = pl.b[qi];
     if (Tq == 0) continue;
-    const bool hash = Tq <= 2 * BK_F;
+    const bool hash = Tq <= BK_G;
     const uint32_t c0 = bs << A.bshift;
     const uint32_t cend = (uint32_t)min((uint64_t)A.nx, (uint64_t)be << A.bshift);
-    // dense sub-ranges [d0, d0 + P_CHUNK) of a heavy bucket (one range unless the bucket is wider)
-    const bool narrow = hash || width <= P_CHUNK;
-    for (uint32_t d0 = c0; d0 < cend; d0 += narrow ? (cend - c0) : P_CHUNK) {
-      const uint32_t d1 = narrow ? cend : min(cend, d0 + P_CHUNK);
-      const bool dense = !hash;
+    const bool narrow = hash || width <= dcap;
+    for (uint32_t d0 = c0; d0 < cend; d0 += narrow ? (cend - c0) : dcap) {
+      const uint32_t d1 = narrow ? cend : min(cend, d0 + dcap);
       uint32_t cap = hash ? pow2_at_least(max(2u * Tq, 64u)) : 0u;
       ZHash h{tab, tab + PB_CAP, cap - 1};
       auto load = [&](uint32_t base) -> uint32_t {  // slices of N(x)[base, base + N); returns chunks
         uint32_t lo = 0, len = 0;
-        if (base + t < xd) {
-          bucket_slice(A, A.p_adj[xo + base + t], bs, be, lo, len);
-          if (!narrow) {
-            uint32_t a0 = lower_bound_u32(A.o_adj + lo, len, d0);
-            uint32_t a1 = a0 + lower_bound_u32(A.o_adj + lo + a0, len - a0, d1);
-            lo += a0;
-            len = a1 - a0;
+        if (cached) {
+          if (t < (int)xd) {
+            if (bs == 0 && be >= A.nb) lo = 0, len = my_len;
+            else lo = my_bo[bs], len = my_bo[be] - lo;
+            lo += my_s0;
           }
+        } else if (base + t < xd) {
+          bucket_slice(A, A.p_adj[xo + base + t], bs, be, lo, len);
+        }
+        if (!narrow && len) {
+          uint32_t a0 = lower_bound_u32(A.o_adj + lo, len, d0);
+          uint32_t a1 = a0 + lower_bound_u32(A.o_adj + lo + a0, len - a0, d1);
+          lo += a0;
+          len = a1 - a0;
         }
         mb.lo[t] = lo;
         mb.len[t] = len;
         return g.scan(nchunks(len), mb.pre);
       };
-      auto inc = [&](uint32_t xp) {
-        if (dense) atomicAdd(&tab[xp - d0], 1u);
-        else h.inc(xp);
-      };
-      auto take = [&](uint32_t xp) {
-        uint32_t c = atomicExch(&tab[xp - d0], 0u);
-        if (c >= 2) {
-          sub_support(A, xp, choose2(c));
-          nup++;
-        }
-      };
-      uint32_t Cw = 0;
-      for (uint32_t base = 0; base < xd; base += N) {
-        uint32_t Cb = load(base);
-        Cw += Cb;
-        walk_chunks(A, t, mb, (int)min((uint32_t)N, xd - base), Cb, inc);
-        __syncthreads();
-      }
-      // wedges of this (sub-)range: exact from the plan, else bounded by the chunks
-      const uint64_t Tw = narrow ? (uint64_t)Tq : (uint64_t)Cw * 32;
-      if (!dense) {  // drain the hash slot by slot
-        for (uint32_t i = t; i < cap; i += N) {
-          uint32_t k = tab[i];
-          if (k) {
-            uint32_t c = tab[PB_CAP + i];
-            if (c >= 2) {
-              sub_support(A, k - 1, choose2(c));
-              nup++;
-            }
-            tab[i] = 0;
-            tab[PB_CAP + i] = 0;
-          }
-        }
-      } else if (Tw >= (d1 - d0) / 2) {  // dense and crowded: scan the counters
-        for (uint32_t i = t; i < d1 - d0; i += N) {
-          uint32_t c = tab[i];
-          if (c) {
-            tab[i] = 0;
-            if (c >= 2) {
-              sub_support(A, d0 + i, choose2(c));
-              nup++;
-            }
-          }
-        }
-      } else if (xd <= (uint32_t)N) {  // dense and sparse: walk the wedges again
-        walk_chunks(A, t, mb, (int)xd, Cw, take);
-      } else {
+      auto walk_all = [&](auto &&f) -> uint32_t {
+        uint32_t Cw = 0;
         for (uint32_t base = 0; base < xd; base += N) {
-          uint32_t Cb = load(base);
-          walk_chunks(A, t, mb, (int)min((uint32_t)N, xd - base), Cb, take);
+          uint32_t C = (base == 0 || !cached) ? load(base) : 0u;
+          Cw += C;
+          walk_slices(A, t, mb, (int)min((uint32_t)N, xd - base), C, f);
           __syncthreads();
+          if (cached) break;
+        }
+        return Cw;
+      };
+      if (hash) {
+        walk_all([&](uint32_t xp) { h.inc(xp); });
+        for (uint32_t i = 4 * t; i < cap; i += 4 * N) {  // drain four slots at a time
+          uint4 k = *(uint4 *)&tab[i];
+          if ((k.x | k.y | k.z | k.w) == 0u) continue;
+          uint4 c = *(uint4 *)&tab[PB_CAP + i];
+          uint32_t kk[4] = {k.x, k.y, k.z, k.w}, cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+          for (int u = 0; u < 4; u++)
+            if (cc[u] >= 2) sub_support(A, kk[u] - 1, choose2(cc[u])), nup++;
+          *(uint4 *)&tab[i] = make_uint4(0u, 0u, 0u, 0u);
+          *(uint4 *)&tab[PB_CAP + i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+      } else if (w16) {
+        const uint32_t Cw = walk_all([&](uint32_t xp) {
+          uint32_t o = xp - d0;
+          atomicAdd(&tab[o >> 1], 1u << ((o & 1) * 16));
+        });
+        const uint64_t Tw = narrow ? (uint64_t)Tq : (uint64_t)Cw * 32;
+        if (Tw >= (d1 - d0) / 2 || !cached) {  // crowded (or slices not kept): scan the counters
+          nup += drain_dense<true>(A, tab, d0, d1 - d0, t, N);
+        } else {  // sparse: walk the wedges again, the first visitor takes the count
+          walk_slices(A, t, mb, (int)xd, Cw, [&](uint32_t xp) {
+            uint32_t o = xp - d0, sh = (o & 1) * 16;
+            uint32_t c = (atomicAnd(&tab[o >> 1], ~(0xffffu << sh)) >> sh) & 0xffffu;
+            if (c >= 2) sub_support(A, xp, choose2(c)), nup++;
+          });
+        }
+      } else {
+        const uint32_t Cw = walk_all([&](uint32_t xp) { atomicAdd(&tab[xp - d0], 1u); });
+        const uint64_t Tw = narrow ? (uint64_t)Tq : (uint64_t)Cw * 32;
+        if (Tw >= (d1 - d0) / 2 || !cached) {
+          nup += drain_dense<false>(A, tab, d0, d1 - d0, t, N);
+        } else {
+          walk_slices(A, t, mb, (int)xd, Cw, [&](uint32_t xp) {
+            uint32_t c = atomicExch(&tab[xp - d0], 0u);
+            if (c >= 2) sub_support(A, xp, choose2(c)), nup++;
+          });
         }
       }
       __syncthreads();
@@ -852,6 +880,8 @@ __global__ void k_fd_segs(FDArgs A, uint32_t nx, const uint32_t *part, uint32_t 
   }
 }
 
+// the T wedges of the slices in mb in flattened order (the partitioned slices
+// are short, so one lane per wedge beats whole-warp chunks here)
 template <class Grp, int N, class F>
 __device__ __forceinline__ void fd_walk(const FDArgs &A, const Grp &g, const FMid<N> &mb, uint32_t T, F &&f) {
   for (uint32_t w = g.rank(); w < T; w += N) {
@@ -958,9 +988,9 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
       for (uint32_t bi = 0; bi < nbig; bi++) {
         uint32_t x = lbig[bi];
         uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
+        if (threadIdx.x == 0) my_wedges += A.w_fd[x];
         for (uint32_t b0 = 0; b0 < xd; b0 += FT) {
           uint32_t T = fd_load(A, p, xo, xd, b0, bg, bmb);
-          if (threadIdx.x == 0) my_wedges += T;
           fd_walk(A, bg, bmb, T, [&](uint32_t xp) {
             if (ld_state(&A.state[xp]) == ST_ALIVE) atomicAdd(&cnt[A.loc[xp]], 1u);
           });
@@ -1142,7 +1172,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   // per-round trace (env PBNG_TRACE=<file>): one line per coarse round
   struct Trace {
     FILE *f = nullptr;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     ~Trace() {
       if (f) fclose(f);
       for (auto &e : ev)
@@ -1196,6 +1226,28 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       if (g) cudaGraphDestroy(g);
     }
   } gh;
+  // hc: host copies of the class sizes (grids sized to them, empty classes
+  // skipped), or null for the fixed grids of graph-captured rounds
+  // (ev: optional events recorded after the warp and the group class)
+  auto launch_classes = [&](cudaStream_t st, unsigned *cnt, const unsigned *hc, cudaEvent_t *ev) {
+    if (!hc || hc[PC_WARP]) {
+      unsigned gw = hc ? grid_for((size_t)hc[PC_WARP] * 32, PWT, 6 * sms) : 6 * sms;
+      k_peel_warp<<<gw, PWT, wsm, st>>>(PA, plists + (size_t)PC_WARP * nx, cnt + PC_WARP);
+      CK_LAUNCH();
+    }
+    if (ev) CK(cudaEventRecord(ev[0], st));
+    if (!hc || hc[PC_GROUP]) {
+      unsigned gg = hc ? std::min<unsigned>((hc[PC_GROUP] + 1) / 2, 3 * sms) : 3 * sms;
+      k_peel_group<<<gg, 2 * QGT, peel_group_smem(), st>>>(PA, plists + (size_t)PC_GROUP * nx, cnt + PC_GROUP);
+      CK_LAUNCH();
+    }
+    if (ev) CK(cudaEventRecord(ev[1], st));
+    if (!hc || hc[PC_BLOCK]) {
+      unsigned gb = hc ? std::min<unsigned>(hc[PC_BLOCK], PB_PER_SM * sms) : PB_PER_SM * sms;
+      k_peel_block<<<gb, PBT, peel_block_smem(), st>>>(PA, blist, cnt + PC_BLOCK);
+      CK_LAUNCH();
+    }
+  };
   auto prep_args = [&](const uint32_t *F, uint32_t nf, uint32_t pi, ull *sum_w, unsigned *counts, unsigned *touched_n) {
     PrepArgs R{};
     R.frontier = F;
@@ -1240,6 +1292,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const uint64_t launches0 = g_launches;  // captured launches are counted per execution
     for (int half = 0; half < 2; half++) {
       uint32_t *F = half == 0 ? front : front2, *Nx = half == 0 ? front2 : front;
       k_round_reset<<<1, 1, 0, cs>>>(Rd);
@@ -1247,14 +1300,13 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       R.nf_dev = &Rd->nf;
       R.pi_dev = &Rd->pi;
       k_prep<<<16 * sms, T, 0, cs>>>(R);
-      k_peel_warp<<<6 * sms, PWT, wsm, cs>>>(PA, plists + (size_t)PC_WARP * nx, Rd->counts + PC_WARP);
-      k_peel_group<<<3 * sms, 2 * QGT, peel_group_smem(), cs>>>(PA, plists + (size_t)PC_GROUP * nx, Rd->counts + PC_GROUP);
-      k_peel_block<<<PB_PER_SM * sms, PBT, peel_block_smem(), cs>>>(PA, blist, Rd->counts + PC_BLOCK);
+      launch_classes(cs, Rd->counts, nullptr, nullptr);
       if (prm.compact)
         k_compact<<<4 * sms, T, 0, cs>>>(touched, &Rd->touched_n, o_off, o_adj, o_len, ytouch, dead, state, boff, nb, bshift);
       k_scan_frontier<<<cap, T, 0, cs>>>(alist, 0, state, sup, init, &rs->theta_hi, 0, Nx, &Rd->nn, &Rd->na);
       k_round_end<<<1, 1, 0, cs>>>(Rd, h, half == 1);
     }
+    g_launches = launches0;
     cudaGraph_t captured = nullptr;
     cudaError_t le = cudaGetLastError(), ce = cudaStreamEndCapture(cs, &captured);
     cudaStreamDestroy(cs);
@@ -1373,7 +1425,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       CK(cudaMemcpyAsync(&hr, Rd, sizeof(RoundDev), cudaMemcpyDeviceToHost, a.st));
       CK(cudaStreamSynchronize(a.st));
       cur_final = hr.part_work;
-      g_launches += (hr.iters - it0) * 2 * (prm.compact ? 8 : 7);
+      g_launches += (hr.iters - it0) * 2 * (7 + (prm.compact ? 1 : 0));
       rounds = hr.rounds;
       wedges_cd = hr.tot_wedges;
       exp_cd = hr.tot_exp;
@@ -1420,21 +1472,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
         front_cd += nf;
         if (trace) CK(cudaEventRecord(tev[0], a.st));
         g_prof.begin(PROF_PEEL);
-        if (hc[2 + PC_WARP]) {
-          k_peel_warp<<<grid_for((size_t)hc[2 + PC_WARP] * 32, PWT, 6 * sms), PWT, wsm, a.st>>>(PA, plists + (size_t)PC_WARP * nx,
-                                                                                                dc + 3 + PC_WARP);
-          CK_LAUNCH();
-        }
-        if (hc[2 + PC_GROUP]) {
-          k_peel_group<<<std::min<unsigned>((hc[2 + PC_GROUP] + 1) / 2, 3 * sms), 2 * QGT, peel_group_smem(), a.st>>>(
-              PA, plists + (size_t)PC_GROUP * nx, dc + 3 + PC_GROUP);
-          CK_LAUNCH();
-        }
-        if (hc[2 + PC_BLOCK]) {
-          k_peel_block<<<std::min<unsigned>(hc[2 + PC_BLOCK], PB_PER_SM * sms), PBT, peel_block_smem(), a.st>>>(
-              PA, blist, dc + 3 + PC_BLOCK);
-          CK_LAUNCH();
-        }
+        launch_classes(a.st, dc + 3, hc + 2, trace ? tev + 2 : nullptr);
         g_prof.end();
         if (trace) CK(cudaEventRecord(tev[1], a.st));
       }
@@ -1447,10 +1485,16 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       CK_LAUNCH();
       uint32_t nf_next = fetch(a, dc + 1);
       if (trace) {
-        float ms = 0.f;
-        if (!do_recount) CK(cudaEventElapsedTime(&ms, tev[0], tev[1]));
-        fprintf(trace, "%d %u %llu %u %u %u %u %llu %llu %d %.4f\n", side, pi, (unsigned long long)rounds, nf,
-                hc[2 + PC_WARP], hc[2 + PC_GROUP], hc[2 + PC_BLOCK], hw, hw2[2], (int)do_recount, ms);
+        float ms = 0.f, m1 = 0.f, m2 = 0.f;
+        if (!do_recount) {
+          CK(cudaEventElapsedTime(&ms, tev[0], tev[1]));
+          CK(cudaEventElapsedTime(&m1, tev[0], tev[2]));
+          CK(cudaEventElapsedTime(&m2, tev[2], tev[3]));
+        }
+        // side range round |active| items(warp group block) wedges maxW recount ms(peel warp group block)
+        fprintf(trace, "%d %u %llu %u %u %u %u %llu %llu %d %.4f %.4f %.4f %.4f\n", side, pi, (unsigned long long)rounds, nf,
+                hc[2 + PC_WARP], hc[2 + PC_GROUP], hc[2 + PC_BLOCK], hw, hw2[2], (int)do_recount, ms, m1, m2,
+                ms - m1 - m2);
       }
       nf = nf_next;
       std::swap(front, front2);

@@ -37,6 +37,51 @@ __device__ __forceinline__ int seg_of(const uint32_t *pre, int n, uint32_t w) {
   return lo;
 }
 
+__device__ __forceinline__ uint32_t nchunks(uint32_t len) { return (len + 31) >> 5; }
+
+// Wedge walk over nseg slices of an adjacency array (slice i starts at lo[i]
+// and holds len[i] entries); pre is the exclusive prefix of the slices'
+// 32-entry chunk counts (pre[nseg] = C, the total).  The NT/32 warps of the
+// group take contiguous runs of chunks: a warp finds the slice of its first
+// chunk by binary search and then advances slice by slice, so a chunk costs a
+// few warp instructions and its 32 reads are coalesced; four chunks are in
+// flight per warp.  f(i, pos, v) is called for every entry, v = adj[pos].
+template <int NT, class F>
+__device__ __forceinline__ void walk_chunks(const uint32_t *__restrict__ adj, int rank, const uint32_t *lo,
+                                            const uint32_t *len, const uint32_t *pre, int nseg, uint32_t C, F &&f) {
+  constexpr uint32_t NW = NT / 32;
+  const uint32_t lane = rank & 31, wid = rank >> 5;
+  const uint32_t per = (C + NW - 1) / NW;
+  uint32_t c = wid * per;
+  const uint32_t ce = min(C, c + per);
+  if (c >= ce) return;
+  int i = seg_of(pre, nseg, c);
+  for (; c + 3 < ce; c += 4) {
+    uint32_t a[4];
+    int si[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      while (pre[i + 1] <= c + u) i++;
+      uint32_t off = ((c + u - pre[i]) << 5) + lane;
+      si[u] = i;
+      ok[u] = off < len[i];
+      a[u] = lo[i] + off;
+    }
+    uint32_t v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) v[u] = ok[u] ? __ldg(&adj[a[u]]) : 0u;
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      if (ok[u]) f(si[u], a[u], v[u]);
+  }
+  for (; c < ce; c++) {
+    while (pre[i + 1] <= c) i++;
+    uint32_t off = ((c - pre[i]) << 5) + lane;
+    if (off < len[i]) f(i, lo[i] + off, __ldg(&adj[lo[i] + off]));
+  }
+}
+
 // ------------------------------------------------------------ groups
 struct WarpGrp {
   static constexpr int N = 32;

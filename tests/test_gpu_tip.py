@@ -151,6 +151,59 @@ def test_tip_bucket_widths(pbng, shift, graph_rounds):
         assert np.array_equal(got, want)
 
 
+def repeat_graph():
+    """200k x 1k graph whose vertices share two neighbours in blocks of 5000:
+    one block inside a single 2^14-id bucket, one spread over all buckets."""
+    if "rep" not in _BK_GRAPH:
+        rng = np.random.default_rng(91)
+        nu, nv = 200000, 1000
+        eu = [np.arange(nu), np.arange(0, nu, 3)]
+        ev = [rng.integers(4, nv, size=nu), rng.integers(4, nv, size=len(range(0, nu, 3)))]
+        for S, ys in ((np.arange(100, 5100), (0, 1)), (np.arange(0, nu, 40)[:5000], (2, 3))):
+            for y in ys:
+                eu.append(S)
+                ev.append(np.full(S.size, y))
+        key = np.unique(np.concatenate(eu).astype(np.int64) * nv + np.concatenate(ev))
+        g = gen.from_edges(nu, nv, key // nv, key % nv)
+        _BK_GRAPH["rep"] = (g, oracle.tip(g, "U"))
+    return _BK_GRAPH["rep"]
+
+
+@pytest.mark.parametrize("shift", [0, 17])
+@pytest.mark.parametrize("graph_rounds", [False, True])
+def test_tip_many_repeated_targets(pbng, shift, graph_rounds):
+    """Block-class vertices whose targets are mostly shared (c >= 2) within
+    one bucket, and spread over all buckets."""
+    g, want = repeat_graph()
+    dg = pbng.to_device(g)
+    for P in (1, 12):
+        got = pbng.as_u64(pbng.tip_decompose(dg, "U", P=P, bucket_shift=shift, graph_rounds=graph_rounds))
+        assert np.array_equal(got, want)
+
+
+def hub_graph():
+    """One U vertex adjacent to all 70k V vertices (2^16 or more neighbours:
+    32-bit dense counters, neighbours read in chunks), 20k U vertices."""
+    if "hub" not in _BK_GRAPH:
+        rng = np.random.default_rng(5)
+        nu, nv = 20000, 70000
+        eu = [np.zeros(nv, np.int64)] + [rng.integers(1, nu, size=nv) for _ in range(2)]
+        ev = [np.arange(nv)] * 3
+        key = np.unique(np.concatenate(eu) * nv + np.concatenate(ev))
+        g = gen.from_edges(nu, nv, key // nv, key % nv)
+        _BK_GRAPH["hub"] = (g, oracle.tip(g, "U"))
+    return _BK_GRAPH["hub"]
+
+
+@pytest.mark.parametrize("graph_rounds", [False, True])
+def test_tip_hub_vertex(pbng, graph_rounds):
+    g, want = hub_graph()
+    dg = pbng.to_device(g)
+    for P in (1, 3, 30):
+        got = pbng.as_u64(pbng.tip_decompose(dg, "U", P=P, graph_rounds=graph_rounds))
+        assert np.array_equal(got, want)
+
+
 def test_tip_explicit_and_random_bounds(pbng):
     name = "chunglu_20k_4k_200k"
     g = GRAPHS[name]
