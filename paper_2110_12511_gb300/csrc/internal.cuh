@@ -144,6 +144,7 @@ struct RangeState {  // device-side state of the weighted selection
   unsigned long long kmin, kmax, wsum;  // key range and total work of the remaining entities
   unsigned long long prefix, below, tgt, est, theta_hi;
   unsigned long long hist[256];
+  unsigned done;  // blocks finished with the current digit
 };
 void set_u64(Arena &a, uint64_t *p, uint64_t v);
 // theta_hi for the remaining entities alist[0..na) with supports sup[] and

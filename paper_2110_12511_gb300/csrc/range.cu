@@ -13,12 +13,21 @@ namespace {
 
 using ull = unsigned long long;
 
-__global__ void k_range_hist(const uint32_t *alist, uint32_t na, const ull *sup, const ull *wl, RangeState *rs, int shift) {
+// One digit of the selection: the work histogram of the digit over the keys
+// that match the prefix so far, then (last block to finish) the digit at
+// which the cumulative work first reaches the target.
+__global__ void __launch_bounds__(256) k_range_pass(const uint32_t *alist, uint32_t na, const ull *sup, const ull *wl,
+                                                    RangeState *rs, int shift, int last) {
   __shared__ ull h[256];
-  h[threadIdx.x] = 0;
+  __shared__ ull wtot[8];
+  __shared__ ull s_cum, s_hd, s_h255;
+  __shared__ int s_d;
+  __shared__ bool s_last;
+  const int t = threadIdx.x;
+  h[t] = 0;
   __syncthreads();
-  ull prefix = rs->prefix;
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < na; j += (size_t)gridDim.x * blockDim.x) {
+  const ull prefix = rs->prefix;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + t; j < na; j += (size_t)gridDim.x * blockDim.x) {
     ull key = sup[alist[j]];
     if (shift + 8 >= 64 || ((key ^ prefix) >> (shift + 8)) == 0) {
       ull w = wl[j];
@@ -26,29 +35,63 @@ __global__ void k_range_hist(const uint32_t *alist, uint32_t na, const ull *sup,
     }
   }
   __syncthreads();
-  if (h[threadIdx.x]) atomicAdd(&rs->hist[threadIdx.x], h[threadIdx.x]);
+  if (h[t]) atomicAdd(&rs->hist[t], h[t]);
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(&rs->done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // inclusive scan of the 256 bins
+  const ull v = __ldcg(&rs->hist[t]);
+  const int lane = t & 31, w = t >> 5;
+  ull inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    ull y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wtot[w] = inc;
+  if (t == 0) s_d = 256;
+  if (t == 255) s_h255 = v;
+  __syncthreads();
+  ull off = 0, total = 0;
+  for (int k = 0; k < 8; k++) {
+    if (k < w) off += wtot[k];
+    total += wtot[k];
+  }
+  inc += off;
+  const ull below = rs->below, tgt = rs->tgt, excl = inc - v;
+  if (below + inc >= tgt && (t == 0 || below + excl < tgt)) {  // the first bin reaching the target
+    s_d = t;
+    s_cum = below + excl;
+    s_hd = v;
+  }
+  __syncthreads();
+  rs->hist[t] = 0;
+  if (t == 0) {
+    int d = s_d;
+    ull cum = s_cum, hd = s_hd;
+    if (d == 256) {  // the target is not reached: take the last digit
+      d = 255;
+      cum = below + total;
+      hd = s_h255;
+    }
+    rs->below = cum;
+    rs->prefix = (prefix & ~(255ull << shift)) | ((ull)d << shift);
+    rs->done = 0;
+    if (last) {
+      rs->est = cum + hd;
+      rs->theta_hi = rs->prefix + 1;
+    }
+  }
 }
 
-// the digit at which the cumulative work first reaches the target
-__global__ void k_range_select(RangeState *rs, int shift, int last) {
-  if (threadIdx.x != 0) return;
-  ull cum = rs->below;
-  int d = 255;
-  for (int i = 0; i < 256; i++) {
-    if (cum + rs->hist[i] >= rs->tgt) {
-      d = i;
-      break;
-    }
-    cum += rs->hist[i];
-  }
-  ull est = cum + rs->hist[d];
-  rs->below = cum;
-  rs->prefix = (rs->prefix & ~(255ull << shift)) | ((ull)d << shift);
-  for (int i = 0; i < 256; i++) rs->hist[i] = 0;
-  if (last) {
-    rs->est = est;
-    rs->theta_hi = rs->prefix + 1;
-  }
+__global__ void k_range_init(RangeState *rs, ull tgt, ull prefix) {
+  rs->tgt = tgt;
+  rs->prefix = prefix;
+  rs->below = 0;
+  rs->done = 0;
 }
 
 __global__ void k_set_u64(ull *p, ull v) { *p = v; }
@@ -68,14 +111,12 @@ uint64_t range_select(Arena &a, RangeState *rs, const uint32_t *alist, uint32_t 
   }
   int hb = 64 - __builtin_clzll(kmin ^ kmax);  // low bits in which keys differ
   uint64_t low = hb >= 64 ? ~0ull : ((1ull << hb) - 1);
-  set_u64(a, (uint64_t *)&rs->tgt, tgt);
-  set_u64(a, (uint64_t *)&rs->prefix, kmin & ~low);
-  set_u64(a, (uint64_t *)&rs->below, 0);
+  k_range_init<<<1, 1, 0, a.st>>>(rs, tgt, kmin & ~low);
+  CK_LAUNCH();
   int top = ((hb - 1) / 8) * 8;
   for (int shift = top; shift >= 0; shift -= 8) {
-    k_range_hist<<<grid_for(na, 256, 4 * num_sms()), 256, 0, a.st>>>(alist, na, (const ull *)sup, (const ull *)wl, rs, shift);
-    CK_LAUNCH();
-    k_range_select<<<1, 32, 0, a.st>>>(rs, shift, shift == 0);
+    k_range_pass<<<grid_for(na, 256, 4 * num_sms()), 256, 0, a.st>>>(alist, na, (const ull *)sup, (const ull *)wl, rs,
+                                                                      shift, shift == 0);
     CK_LAUNCH();
   }
   uint64_t he[2];

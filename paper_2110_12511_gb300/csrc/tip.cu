@@ -21,6 +21,7 @@
 //  peels every vertex whose support equals the running minimum (ties receive
 //  the same number, exactly as one-at-a-time peeling with the clamp).
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -235,24 +236,28 @@ __global__ void __launch_bounds__(2 * QGT) k_peel_group(PeelArgs A, const uint64
 
 size_t peel_group_smem() { return 2 * align16(QG_CAP * 8 + sizeof(PMid<QGT>) + (QGT / 32 + 2) * 4); }
 
-// Shared hash whose keys are stored as id + 1, so that an all-zero table is
-// empty and the same memory can serve as zeroed dense counters.
-struct ZHash {
-  uint32_t *key, *val;
+// Shared hash with one 64-bit slot per target: (id + 1) << 32 | count, zero
+// = empty, so that an insert is a single compare-and-swap and a repeat a
+// single add, and an all-zero table doubles as zeroed dense counters.
+struct WHash {
+  unsigned long long *slot;
   uint32_t mask;
   __device__ __forceinline__ void inc(uint32_t id) const {
-    uint32_t k = id + 1, h = hash32(id) & mask;
-    volatile uint32_t *vk = key;
+    const uint32_t tag = id + 1;
+    uint32_t h = hash32(id) & mask;
+    volatile unsigned long long *vs = slot;
     for (;;) {
-      uint32_t cur = vk[h];
-      if (cur == k) break;
+      unsigned long long cur = vs[h];
       if (cur == 0) {
-        uint32_t prev = atomicCAS(&key[h], 0u, k);
-        if (prev == 0 || prev == k) break;
+        cur = atomicCAS(&slot[h], 0ull, ((unsigned long long)tag << 32) | 1ull);
+        if (cur == 0) return;
+      }
+      if ((uint32_t)(cur >> 32) == tag) {
+        atomicAdd(&slot[h], 1ull);
+        return;
       }
       h = (h + 1) & mask;
     }
-    atomicAdd(&val[h], 1u);
   }
 };
 
@@ -409,7 +414,7 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
     for (uint32_t d0 = c0; d0 < cend; d0 += narrow ? (cend - c0) : dcap) {
       const uint32_t d1 = narrow ? cend : min(cend, d0 + dcap);
       uint32_t cap = hash ? pow2_at_least(max(2u * Tq, 64u)) : 0u;
-      ZHash h{tab, tab + PB_CAP, cap - 1};
+      WHash h{(unsigned long long *)tab, cap - 1};
       auto load = [&](uint32_t base) -> uint32_t {  // slices of N(x)[base, base + N); returns chunks
         uint32_t lo = 0, len = 0;
         if (cached) {
@@ -444,16 +449,12 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
       };
       if (hash) {
         walk_all([&](uint32_t xp) { h.inc(xp); });
-        for (uint32_t i = 4 * t; i < cap; i += 4 * N) {  // drain four slots at a time
-          uint4 k = *(uint4 *)&tab[i];
-          if ((k.x | k.y | k.z | k.w) == 0u) continue;
-          uint4 c = *(uint4 *)&tab[PB_CAP + i];
-          uint32_t kk[4] = {k.x, k.y, k.z, k.w}, cc[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-          for (int u = 0; u < 4; u++)
-            if (cc[u] >= 2) sub_support(A, kk[u] - 1, choose2(cc[u])), nup++;
-          *(uint4 *)&tab[i] = make_uint4(0u, 0u, 0u, 0u);
-          *(uint4 *)&tab[PB_CAP + i] = make_uint4(0u, 0u, 0u, 0u);
+        for (uint32_t i = 2 * t; i < cap; i += 2 * N) {  // drain two slots at a time
+          uint4 q = *(uint4 *)&tab[2 * i];  // slots i, i + 1: (count, tag) words
+          if ((q.x | q.y | q.z | q.w) == 0u) continue;
+          if (q.x >= 2) sub_support(A, q.y - 1, choose2(q.x)), nup++;
+          if (q.z >= 2) sub_support(A, q.w - 1, choose2(q.z)), nup++;
+          *(uint4 *)&tab[2 * i] = make_uint4(0u, 0u, 0u, 0u);
         }
       } else if (w16) {
         const uint32_t Cw = walk_all([&](uint32_t xp) {
@@ -1172,7 +1173,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   // per-round trace (env PBNG_TRACE=<file>): one line per coarse round
   struct Trace {
     FILE *f = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[7] = {};
     ~Trace() {
       if (f) fclose(f);
       for (auto &e : ev)
@@ -1338,6 +1339,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   uint32_t P = prm.P;
   while (na > 0) {
     // ---- remaining list (drop peeled vertices)
+    auto rwall0 = std::chrono::steady_clock::now();
     if (pi > 0) {
       CK(cudaMemsetAsync(dc + 7, 0, 4, a.st));
       k_compact_list<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, alist2, dc + 7);
@@ -1437,9 +1439,14 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     k_scan_frontier<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, sup, init, &rs->theta_hi, 1, front, dc);
     CK_LAUNCH();
     uint32_t nf = fetch(a, dc);
+    if (trace)  // range line: side range |remaining| |first active set| ms to pick the range
+      fprintf(trace, "R %d %u %u %u %.4f\n", side, pi, na, nf,
+              std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - rwall0).count());
     // ---- peeling rounds (Alg. 4 l.10-13)
     while (nf > 0) {
       rounds++;
+      auto wall0 = std::chrono::steady_clock::now();
+      if (trace) CK(cudaEventRecord(tev[4], a.st));
       CK(cudaMemsetAsync(dc + 1, 0, 6 * 4, a.st));
       CK(cudaMemsetAsync(sumw, 0, 24, a.st));
       PrepArgs R = prep_args(front, nf, pi, sumw, dc + 3, dc + 2);
@@ -1474,27 +1481,34 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
         g_prof.begin(PROF_PEEL);
         launch_classes(a.st, dc + 3, hc + 2, trace ? tev + 2 : nullptr);
         g_prof.end();
-        if (trace) CK(cudaEventRecord(tev[1], a.st));
       }
+      if (trace) CK(cudaEventRecord(tev[1], a.st));  // (re-count rounds: end of the re-count)
       if (prm.compact) {
         k_compact<<<4 * sms, T, 0, a.st>>>(touched, dc + 2, o_off, o_adj, o_len, ytouch, dead, state, boff, nb, bshift);
         CK_LAUNCH();
       }
+      if (trace) CK(cudaEventRecord(tev[5], a.st));
       // next active set (dc[1] was cleared with the class counters)
       k_scan_frontier<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, sup, init, &rs->theta_hi, 0, front2, dc + 1);
       CK_LAUNCH();
+      if (trace) CK(cudaEventRecord(tev[6], a.st));
       uint32_t nf_next = fetch(a, dc + 1);
       if (trace) {
-        float ms = 0.f, m1 = 0.f, m2 = 0.f;
+        float ms = 0.f, m1 = 0.f, m2 = 0.f, mp = 0.f, mc = 0.f, mf = 0.f;
         if (!do_recount) {
           CK(cudaEventElapsedTime(&ms, tev[0], tev[1]));
           CK(cudaEventElapsedTime(&m1, tev[0], tev[2]));
           CK(cudaEventElapsedTime(&m2, tev[2], tev[3]));
+          CK(cudaEventElapsedTime(&mp, tev[4], tev[0]));
         }
-        // side range round |active| items(warp group block) wedges maxW recount ms(peel warp group block)
-        fprintf(trace, "%d %u %llu %u %u %u %u %llu %llu %d %.4f %.4f %.4f %.4f\n", side, pi, (unsigned long long)rounds, nf,
-                hc[2 + PC_WARP], hc[2 + PC_GROUP], hc[2 + PC_BLOCK], hw, hw2[2], (int)do_recount, ms, m1, m2,
-                ms - m1 - m2);
+        CK(cudaEventElapsedTime(&mc, tev[1], tev[5]));
+        CK(cudaEventElapsedTime(&mf, tev[5], tev[6]));
+        double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+        // side range round |active| items(warp group block) wedges maxW recount
+        // ms: peel (warp group block) prep+sync compact scan wall
+        fprintf(trace, "%d %u %llu %u %u %u %u %llu %llu %d %.4f %.4f %.4f %.4f %.4f %.4f %.4f %.4f\n", side, pi,
+                (unsigned long long)rounds, nf, hc[2 + PC_WARP], hc[2 + PC_GROUP], hc[2 + PC_BLOCK], hw, hw2[2],
+                (int)do_recount, ms, m1, m2, ms - m1 - m2, mp, mc, mf, wall);
       }
       nf = nf_next;
       std::swap(front, front2);
