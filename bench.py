@@ -231,8 +231,26 @@ def run_extra(args):
         dgs = [pbng.to_device(g, dev) for g in gs]
         res.update({"graphs": n, "edges": int(sum(g.m for g in gs))})
         P = 150
-        pbng.tip_decompose_batch(dgs, "U", P=P)
-        tb, (_, stb) = timed(lambda: pbng.tip_decompose_batch(dgs, "U", P=P, with_stats=True), dev, flush)
+        bkw, size = {}, n
+        if args.autotune:  # schedule on a sample, then the batch size (not timed)
+            from paper_2110_12511_gb300 import autotune
+            cfg, _, _ = autotune.tune_batch_schedule(dgs, "U", P=P)
+            size, _ = autotune.tune_batch(dgs, "U", P=P, sizes=(1024, 2048, n), cfg=cfg)
+            bkw = autotune.split(cfg)
+            res.update({"schedule": cfg, "batch_size": size})
+        elif args.graph_rounds:
+            bkw = {"graph_rounds": True}
+            res["schedule"] = bkw
+
+        def batched():
+            stats = None
+            for i in range(0, n, size):
+                _, s1 = pbng.tip_decompose_batch(dgs[i:i + size], "U", P=P, with_stats=True, **bkw)
+                stats = s1 if stats is None else {k: stats[k] + s1[k] for k in ("wedges_count", "wedges_cd", "wedges_fd")}
+            return None, stats
+
+        batched()
+        tb, (_, stb) = timed(batched, dev, flush)
         def one_by_one():
             w = 0
             for d in dgs:
@@ -273,6 +291,8 @@ def main():
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--graph-rounds", action="store_true", help="coarse rounds as a CUDA graph with a device loop")
     ap.add_argument("--no-recount", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the coarse-peel schedule per side with the autotuner before timing (not timed)")
     args = ap.parse_args()
     ws, rank, local = dist_info()
     if args.impl == "reference":
@@ -302,10 +322,19 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
     kw = {"graph_rounds": args.graph_rounds, "recount": not args.no_recount}
+    kws = {"U": dict(kw), "V": dict(kw)}
+    tuned = None
+    if args.autotune:
+        from paper_2110_12511_gb300 import autotune
+        tuned = {}
+        for side in ("U", "V"):
+            cfg, _, _ = autotune.tune_tip(dg, side, P=args.P, reps=1)
+            tuned[side] = cfg
+            kws[side] = dict(kw, **autotune.split(cfg))
 
     def step():
-        su = pbng.tip_decompose(dg, "U", P=args.P, with_stats=True, **kw)[1]
-        sv = pbng.tip_decompose(dg, "V", P=args.P, with_stats=True, **kw)[1]
+        su = pbng.tip_decompose(dg, "U", P=args.P, with_stats=True, **kws["U"])[1]
+        sv = pbng.tip_decompose(dg, "V", P=args.P, with_stats=True, **kws["V"])[1]
         return su, sv
 
     for _ in range(args.warmup):
@@ -372,13 +401,13 @@ def main():
     e2e_t = []
     e2e_w = 0
     if not args.no_e2e:
-        pbng.tip_decompose_host(hg, "U", P=args.P, **kw)
+        pbng.tip_decompose_host(hg, "U", P=args.P, **kws["U"])
     for _ in range(0 if args.no_e2e else max(1, args.steps)):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        _, su = pbng.tip_decompose_host(hg, "U", P=args.P, with_stats=True, **kw)
-        _, sv = pbng.tip_decompose_host(hg, "V", P=args.P, with_stats=True, **kw)
+        _, su = pbng.tip_decompose_host(hg, "U", P=args.P, with_stats=True, **kws["U"])
+        _, sv = pbng.tip_decompose_host(hg, "V", P=args.P, with_stats=True, **kws["V"])
         e2e_t.append(time.perf_counter() - t0)
         e2e_w += tip_wedges(su) + tip_wedges(sv)
     tt = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
@@ -404,7 +433,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic (seeded Chung-Lu generator)",
             "config": {"workload": WORKLOAD_DESC, "name": WORKLOAD, "P": args.P, "sides": "U,V",
-                       "graph_rounds": args.graph_rounds, "recount": not args.no_recount,
+                       "graph_rounds": args.graph_rounds, "recount": not args.no_recount, "schedule": tuned,
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write)", "nu": g.nu, "nv": g.nv, "m": g.m,
                        "wedges_per_step": wedges_step,

@@ -84,8 +84,13 @@ typedef struct pbng_opts {
   uint32_t n_bounds_out;   /* capacity of bounds_out; the count written is stats->parts_used - 1
                               (at most this many are stored) */
   uint32_t bucket_shift;   /* tip: the coarse peel cuts the peeled side's ids into buckets of
-                              2^bucket_shift ids (at most 512 buckets); 0 (default) = automatic,
-                              else 14..30 (raised when needed); results are identical */
+                              2^bucket_shift ids (at most 512 buckets); 0 (default) = automatic
+                              (15, raised when needed), else 14..30; results are identical */
+  /* tip coarse-peel schedule (0 = default; results are identical for every value):
+     an active vertex with W wedges is peeled by one warp when W <= warp_max_w (at most 512,
+     default 512), by a 256-thread group when W <= group_max_w (warp_max_w..2048, default 2048),
+     else by blocks, one per item of at least item_w wedges (>= 4096, default 32768) */
+  uint32_t warp_max_w, group_max_w, item_w;
 } pbng_opts;
 
 typedef struct pbng_stats {

@@ -38,7 +38,8 @@ class Opts(ctypes.Structure):
                 ("graph_rounds", ctypes.c_int), ("timeout_ns", ctypes.c_uint64), ("stream", ctypes.c_void_p),
                 ("mlp_params", ctypes.c_void_p), ("mlp_hidden", ctypes.c_uint32), ("mlp_out", ctypes.c_uint32),
                 ("bounds_out", ctypes.c_void_p), ("n_bounds_out", ctypes.c_uint32),
-                ("bucket_shift", ctypes.c_uint32)]
+                ("bucket_shift", ctypes.c_uint32), ("warp_max_w", ctypes.c_uint32),
+                ("group_max_w", ctypes.c_uint32), ("item_w", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -145,11 +146,18 @@ def to_device(g, device="cuda") -> DeviceGraph:
     return DeviceGraph(int(g.nu), int(g.nv), off, adj)
 
 
+SCHEDULE_KEYS = ("bucket_shift", "warp_max_w", "group_max_w", "item_w")
+
+
 def _opts(stream=None, bounds=None, recount=True, compact=True, mem=MEM_DEVICE, graph_rounds=False, keep=None,
-          mlp=None, bounds_out=None, bucket_shift=0):
+          mlp=None, bounds_out=None, bucket_shift=0, schedule=None):
     o = Opts()
     lib().pbng_opts_init(ctypes.byref(o))
     o.bucket_shift = int(bucket_shift)
+    for k, v in (schedule or {}).items():  # coarse-peel schedule (see autotune.py)
+        if k not in SCHEDULE_KEYS:
+            raise ValueError(f"unknown schedule key {k}")
+        setattr(o, k, int(v))
     o.recount = int(bool(recount))
     o.compact = int(bool(compact))
     o.mem = mem
@@ -207,7 +215,7 @@ def _side(side) -> int:
 
 
 def tip_decompose(dg: DeviceGraph, side="U", P=150, bounds=None, recount=True, compact=True, graph_rounds=False,
-                  stream=None, with_stats=False, mlp=None, bounds_out=None, bucket_shift=0):
+                  stream=None, with_stats=False, mlp=None, bounds_out=None, bucket_shift=0, schedule=None):
     """Tip numbers of one side (two-phase PBNG, Sec. 3.1-3.2).
 
     bounds: explicit upper bounds; mlp: (params, hidden, out) of the learned
@@ -218,7 +226,7 @@ def tip_decompose(dg: DeviceGraph, side="U", P=150, bounds=None, recount=True, c
     out = torch.empty(max(n, 1), dtype=torch.int64, device=dg.u_off.device)
     keep = []
     o = _opts(stream, bounds, recount, compact, graph_rounds=graph_rounds, keep=keep, mlp=mlp, bounds_out=bounds_out,
-              bucket_shift=bucket_shift)
+              bucket_shift=bucket_shift, schedule=schedule)
     st = Stats()
     g = dg.c_struct()
     rc = lib().pbng_tip_decompose(ctypes.byref(g), s, int(P), out.data_ptr(), ctypes.byref(o), ctypes.byref(st))
@@ -277,7 +285,8 @@ def tip_decompose_host(g, side="U", P=150, with_stats=False, **kw):
     n = g.nu if s == SIDE_U else g.nv
     out = np.zeros(max(n, 1), dtype=np.uint64)
     o = _opts(kw.get("stream"), kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), mem=MEM_HOST,
-              graph_rounds=kw.get("graph_rounds", False), keep=[])
+              graph_rounds=kw.get("graph_rounds", False), keep=[], bucket_shift=kw.get("bucket_shift", 0),
+              schedule=kw.get("schedule"))
     st = Stats()
     cg = Bigraph(int(g.nu), int(g.nv), adj.size, off.ctypes.data, adj.ctypes.data if adj.size else 0)
     rc = lib().pbng_tip_decompose(ctypes.byref(cg), s, int(P), out.ctypes.data, ctypes.byref(o), ctypes.byref(st))
@@ -307,7 +316,9 @@ def tip_decompose_batch(dgs, side="U", P=150, stream=None, with_stats=False, **k
     outs = [torch.empty(max(d.nu if s == SIDE_U else d.nv, 1), dtype=torch.int64, device=d.u_off.device) for d in dgs]
     ptrs = (ctypes.c_void_p * max(n, 1))(*[o.data_ptr() for o in outs])
     keep = []
-    o = _opts(stream, kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), keep=keep)
+    o = _opts(stream, kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), keep=keep,
+              graph_rounds=kw.get("graph_rounds", False), bucket_shift=kw.get("bucket_shift", 0),
+              schedule=kw.get("schedule"))
     st = Stats()
     rc = lib().pbng_tip_decompose_batch(gs, n, s, int(P), ptrs, ctypes.byref(o), ctypes.byref(st))
     _check(rc, "pbng_tip_decompose_batch")

@@ -108,6 +108,14 @@ TipParams tip_params(uint32_t P, const pbng_opts &o) {
   p.graph_rounds = o.graph_rounds;
   if (o.bucket_shift && (o.bucket_shift < 14 || o.bucket_shift > 30)) fail(PBNG_EINVAL, "bucket_shift must be 0 or 14..30");
   p.bucket_shift = o.bucket_shift;
+  {
+    uint32_t wm = o.warp_max_w ? o.warp_max_w : 512, gm = o.group_max_w ? o.group_max_w : 2048;
+    if (wm > 512 || gm > 2048 || gm < wm) fail(PBNG_EINVAL, "need warp_max_w <= group_max_w, warp_max_w <= 512, group_max_w <= 2048");
+    if (o.item_w && o.item_w < 4096) fail(PBNG_EINVAL, "item_w must be 0 or at least 4096");
+    p.warp_max_w = wm;
+    p.group_max_w = gm;
+    p.item_w = o.item_w;
+  }
   p.timeout_ns = o.timeout_ns ? o.timeout_ns : 10000000000ull;
   p.mlp_params = o.mlp_params;
   p.mlp_hidden = o.mlp_hidden;

@@ -161,6 +161,7 @@ struct TipParams {
   uint32_t n_bounds;
   int recount, compact, graph_rounds;
   uint32_t bucket_shift;  // 0 = automatic
+  uint32_t warp_max_w, group_max_w, item_w;  // coarse-peel schedule, 0 = default
   uint64_t timeout_ns;
   const float *mlp_params;  // learned bounds (bounds_mode == PBNG_BOUNDS_LEARNED)
   uint32_t mlp_hidden, mlp_out;

@@ -245,13 +245,9 @@ struct WHash {
   __device__ __forceinline__ void inc(uint32_t id) const {
     const uint32_t tag = id + 1;
     uint32_t h = hash32(id) & mask;
-    volatile unsigned long long *vs = slot;
-    for (;;) {
-      unsigned long long cur = vs[h];
-      if (cur == 0) {
-        cur = atomicCAS(&slot[h], 0ull, ((unsigned long long)tag << 32) | 1ull);
-        if (cur == 0) return;
-      }
+    for (;;) {  // claim first: one shared operation for a new target
+      unsigned long long cur = atomicCAS(&slot[h], 0ull, ((unsigned long long)tag << 32) | 1ull);
+      if (cur == 0) return;
       if ((uint32_t)(cur >> 32) == tag) {
         atomicAdd(&slot[h], 1ull);
         return;
@@ -260,6 +256,28 @@ struct WHash {
     }
   }
 };
+
+// Shared hash with 32-bit slots (id - c0 + 1) << cb | count, for passes whose
+// id range and counts fit together in 32 bits: twice the slots of WHash.
+struct PHash32 {
+  uint32_t *slot;
+  uint32_t mask, c0, cb;
+  __device__ __forceinline__ void inc(uint32_t id) const {
+    const uint32_t tag = id - c0 + 1;
+    uint32_t h = hash32(id) & mask;
+    for (;;) {  // claim first: one shared operation for a new target
+      uint32_t cur = atomicCAS(&slot[h], 0u, (tag << cb) | 1u);
+      if (cur == 0) return;
+      if ((cur >> cb) == tag) {
+        atomicAdd(&slot[h], 1u);  // the count stays below 2^cb
+        return;
+      }
+      h = (h + 1) & mask;
+    }
+  }
+};
+
+__device__ __forceinline__ uint32_t bit_len(uint64_t v) { return v ? 64 - __clzll(v) : 0; }
 
 // slice of y's current list holding the targets of buckets [bs, be)
 __device__ __forceinline__ void bucket_slice(const PeelArgs &A, uint32_t y, uint32_t bs, uint32_t be, uint32_t &lo,
@@ -298,14 +316,15 @@ struct BPlan {
   uint32_t np;
 };
 
-// drain of dense counters (16-bit pairs or 32-bit) over ids [d0, d0 + n):
-// 16-byte vector reads, zeroed where touched
+// drain of dense counters over ids [d0, d0 + n): 32-bit counters, or 16-bit
+// halves (offset o in word o mod 2^14, half o / 2^14); 16-byte vector reads,
+// zeroed where touched
 template <bool W16>
 __device__ __forceinline__ uint64_t drain_dense(const PeelArgs &A, uint32_t *tab, uint32_t d0, uint32_t n, int t, int N) {
-  constexpr uint32_t PER = W16 ? 8 : 4;  // counters per 16 bytes
   uint64_t nup = 0;
   uint4 *v = (uint4 *)tab;
-  for (uint32_t i = t; i * PER < n; i += N) {
+  const uint32_t words = W16 ? min(n, P_CHUNK) : n;
+  for (uint32_t i = t; i * 4 < words; i += N) {
     uint4 q = v[i];
     if ((q.x | q.y | q.z | q.w) == 0u) continue;
     v[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -313,12 +332,13 @@ __device__ __forceinline__ uint64_t drain_dense(const PeelArgs &A, uint32_t *tab
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       if (!w[k]) continue;
+      uint32_t id = d0 + i * 4 + k;
       if (W16) {
-        uint32_t lo = w[k] & 0xffffu, hi = w[k] >> 16, id = d0 + i * PER + 2 * k;
+        uint32_t lo = w[k] & 0xffffu, hi = w[k] >> 16;
         if (lo >= 2) sub_support(A, id, choose2(lo)), nup++;
-        if (hi >= 2) sub_support(A, id + 1, choose2(hi)), nup++;
+        if (hi >= 2) sub_support(A, id + P_CHUNK, choose2(hi)), nup++;
       } else if (w[k] >= 2) {
-        sub_support(A, d0 + i * PER + k, choose2(w[k]));
+        sub_support(A, id, choose2(w[k]));
         nup++;
       }
     }
@@ -375,16 +395,20 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
   g.scan(t < (int)nbi ? pl.a[t] : 0u, pl.b);
   const bool w16 = xd < 65536u;  // a count never exceeds the number of neighbours
   const uint32_t dcap = w16 ? 2 * P_CHUNK : P_CHUNK;  // ids of one dense pass
+  // 32-bit hash slots when every pass's id offsets and x's counts fit in them
+  const uint32_t cb = bit_len(xd);
+  const bool packed = bit_len((uint64_t)nbi << A.bshift) + cb <= 32;
+  const uint32_t G = packed ? 2 * BK_G : BK_G;  // most wedges of a hash pass (load <= 1/2)
   const uint32_t width = 1u << A.bshift;
   const uint32_t dspan = width <= dcap ? dcap >> A.bshift : 1u;
   if (t == 0) {
     uint32_t s = 0, q = 0;
     while (s < nbi) {
       uint32_t e;
-      if (pl.b[s + 1] - pl.b[s] > BK_G) {
+      if (pl.b[s + 1] - pl.b[s] > G) {
         e = min(nbi, s + dspan);
       } else {  // largest e with wedges(s..e) <= G
-        uint32_t lo = s + 1, hi = nbi, lim = pl.b[s] + BK_G;
+        uint32_t lo = s + 1, hi = nbi, lim = pl.b[s] + G;
         while (lo < hi) {
           uint32_t mid = (lo + hi + 1) >> 1;
           if (pl.b[mid] <= lim) lo = mid;
@@ -407,7 +431,7 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
   for (uint32_t qi = 0; qi < np; qi++) {
     const uint32_t bs = b0 + pl.a[qi], be = b0 + pl.a[qi + 1], Tq = pl.b[qi];
     if (Tq == 0) continue;
-    const bool hash = Tq <= BK_G;
+    const bool hash = Tq <= G;
     const uint32_t c0 = bs << A.bshift;
     const uint32_t cend = (uint32_t)min((uint64_t)A.nx, (uint64_t)be << A.bshift);
     const bool narrow = hash || width <= dcap;
@@ -415,6 +439,7 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
       const uint32_t d1 = narrow ? cend : min(cend, d0 + dcap);
       uint32_t cap = hash ? pow2_at_least(max(2u * Tq, 64u)) : 0u;
       WHash h{(unsigned long long *)tab, cap - 1};
+      PHash32 h32{tab, cap - 1, c0, cb};
       auto load = [&](uint32_t base) -> uint32_t {  // slices of N(x)[base, base + N); returns chunks
         uint32_t lo = 0, len = 0;
         if (cached) {
@@ -447,7 +472,21 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
         }
         return Cw;
       };
-      if (hash) {
+      if (hash && packed) {
+        walk_all([&](uint32_t xp) { h32.inc(xp); });
+        const uint32_t cmask = (1u << cb) - 1u;
+        for (uint32_t i = 4 * t; i < cap; i += 4 * N) {  // drain four slots at a time
+          uint4 q = *(uint4 *)&tab[i];
+          if ((q.x | q.y | q.z | q.w) == 0u) continue;
+          uint32_t v[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            uint32_t c = v[u] & cmask;
+            if (c >= 2) sub_support(A, c0 + (v[u] >> cb) - 1, choose2(c)), nup++;
+          }
+          *(uint4 *)&tab[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+      } else if (hash) {
         walk_all([&](uint32_t xp) { h.inc(xp); });
         for (uint32_t i = 2 * t; i < cap; i += 2 * N) {  // drain two slots at a time
           uint4 q = *(uint4 *)&tab[2 * i];  // slots i, i + 1: (count, tag) words
@@ -456,18 +495,18 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
           if (q.z >= 2) sub_support(A, q.w - 1, choose2(q.z)), nup++;
           *(uint4 *)&tab[2 * i] = make_uint4(0u, 0u, 0u, 0u);
         }
-      } else if (w16) {
+      } else if (w16) {  // offset o counts in word o mod 2^14, half o / 2^14 (consecutive ids, distinct words)
         const uint32_t Cw = walk_all([&](uint32_t xp) {
           uint32_t o = xp - d0;
-          atomicAdd(&tab[o >> 1], 1u << ((o & 1) * 16));
+          atomicAdd(&tab[o & (P_CHUNK - 1)], 1u << ((o >> 14) * 16));
         });
         const uint64_t Tw = narrow ? (uint64_t)Tq : (uint64_t)Cw * 32;
         if (Tw >= (d1 - d0) / 2 || !cached) {  // crowded (or slices not kept): scan the counters
           nup += drain_dense<true>(A, tab, d0, d1 - d0, t, N);
         } else {  // sparse: walk the wedges again, the first visitor takes the count
           walk_slices(A, t, mb, (int)xd, Cw, [&](uint32_t xp) {
-            uint32_t o = xp - d0, sh = (o & 1) * 16;
-            uint32_t c = (atomicAnd(&tab[o >> 1], ~(0xffffu << sh)) >> sh) & 0xffffu;
+            uint32_t o = xp - d0, sh = (o >> 14) * 16;
+            uint32_t c = (atomicAnd(&tab[o & (P_CHUNK - 1)], ~(0xffffu << sh)) >> sh) & 0xffffu;
             if (c >= 2) sub_support(A, xp, choose2(c)), nup++;
           });
         }
@@ -565,6 +604,7 @@ struct PrepArgs {
   unsigned *counts;
   uint32_t nx, nb;
   uint64_t item_w;  // wedges per block-class item (at least)
+  uint32_t warp_max_w, group_max_w;  // class limits (at most QW_MAXW, QG_MAXW)
   uint8_t *lab_alive;  // re-count labels (Sec. 5.1), or null
   const uint32_t *x2lab;
   // dynamic graph updates (Sec. 5.2): the active vertices' entries die this
@@ -605,8 +645,8 @@ __global__ void k_prep(PrepArgs A) {
       atomicAdd(&A.sum_w[1], (ull)xd);
       atomicMax(&A.sum_w[2], (ull)W);
       if (W >= 2) {
-        if (W <= QG_MAXW) {
-          int c = W <= QW_MAXW ? PC_WARP : PC_GROUP;
+        if (W <= A.group_max_w) {
+          int c = W <= A.warp_max_w ? PC_WARP : PC_GROUP;
           unsigned p = atomicAdd(&A.counts[c], 1u);
           A.lists[(size_t)c * A.nx + p] = (uint64_t)x | (W << 32);
         } else {  // K items over equal shares of the target buckets
@@ -1142,7 +1182,8 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   uint32_t *front = a.alloc<uint32_t>(nx), *front2 = a.alloc<uint32_t>(nx);
   uint64_t *plists = a.alloc<uint64_t>((size_t)2 * nx);
   // target buckets and their offsets in every Y list
-  uint32_t bshift = std::max(BK_SHIFT_MIN, prm.bucket_shift);
+  // automatic: 2^15 ids (one 16-bit dense pass per bucket), at least 2^14
+  uint32_t bshift = prm.bucket_shift ? std::max(BK_SHIFT_MIN, prm.bucket_shift) : BK_SHIFT_MIN + 1;
   while (bshift < 31 && (((uint64_t)nx + (1ull << bshift) - 1) >> bshift > NB_MAX ||
                          (uint64_t)ny * ((((uint64_t)nx + (1ull << bshift) - 1) >> bshift) + 1) * 4 > BOFF_BUDGET))
     bshift++;
@@ -1155,7 +1196,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   }
   // block-class items: at most one per active vertex plus one per item_w of
   // its wedges; the wedges of all X vertices together bound a round's
-  uint64_t item_w = ITEM_W, wtot = 0;
+  uint64_t item_w = prm.item_w ? prm.item_w : ITEM_W, wtot = 0;
   {
     ull *d = a.zeros<ull>(1);
     k_sum_sq<<<grid_for(ny, T, cap), T, 0, a.st>>>(o_off, ny, d);
@@ -1266,6 +1307,8 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     R.nx = nx;
     R.nb = nb;
     R.item_w = item_w;
+    R.warp_max_w = std::min(prm.warp_max_w ? prm.warp_max_w : QW_MAXW, QW_MAXW);
+    R.group_max_w = std::min(prm.group_max_w ? prm.group_max_w : QG_MAXW, QG_MAXW);
     R.lab_alive = lab_alive;
     R.x2lab = x2lab;
     R.compact = prm.compact;

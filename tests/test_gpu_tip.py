@@ -261,3 +261,39 @@ def test_malformed_csr_is_rejected(pbng):
         with pytest.raises(pbng.PbngError) as ei:
             pbng.tip_decompose(dg, "U", P=2)
         assert ei.value.code == pbng.PBNG_EINVAL, name
+
+
+@pytest.mark.parametrize("knob,value", [("warp_max_w", 1), ("warp_max_w", 128), ("group_max_w", 512),
+                                        ("item_w", 4096), ("item_w", 1 << 30), ("bucket_shift", 14), ("bucket_shift", 16),
+                                        ("graph_rounds", True)])
+def test_tip_every_schedule_variant(pbng, knob, value):
+    """Every value the autotuner may choose, forced once: identical tip numbers."""
+    from paper_2110_12511_gb300 import autotune as at
+    cfg = dict(at.DEFAULT)
+    cfg[knob] = value
+    if knob == "group_max_w":
+        cfg["warp_max_w"] = 256
+    for name in ("chunglu_5k_1k_50k_planted", "chunglu_20k_4k_200k"):
+        dg = pbng.to_device(GRAPHS[name])
+        for side in ("U", "V"):
+            got = pbng.as_u64(pbng.tip_decompose(dg, side, P=20, **at.split(cfg)))
+            assert np.array_equal(got, oracle_tip(name, side))
+    g, want = bucket_graph()
+    got = pbng.as_u64(pbng.tip_decompose(pbng.to_device(g), "U", P=20, **at.split(cfg)))
+    assert np.array_equal(got, want)
+
+
+def test_autotuner_choice_gives_identical_numbers(pbng, tmp_path):
+    from paper_2110_12511_gb300 import autotune as at
+    name = "chunglu_20k_4k_200k"
+    dg = pbng.to_device(GRAPHS[name])
+    cache = str(tmp_path / "tune.json")
+    cfg, t, table = at.tune_tip(dg, "U", P=40, reps=1, cache=cache)
+    assert at.valid(cfg) and t > 0 and len(table) >= 2
+    got = pbng.as_u64(pbng.tip_decompose(dg, "U", P=40, **at.split(cfg)))
+    assert np.array_equal(got, oracle_tip(name, "U"))
+    cfg2, t2, table2 = at.tune_tip(dg, "U", P=40, cache=cache)  # from the cache
+    assert cfg2 == cfg and table2 == []
+    gs = [gen.batch_graph(1000 + i, scale=0.05) for i in range(8)]
+    size, tb = at.tune_batch([pbng.to_device(g) for g in gs], "U", P=20, sizes=(2, 8), cfg=cfg)
+    assert size in (2, 8) and len(tb) == 2
