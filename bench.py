@@ -268,10 +268,53 @@ def run_extra(args):
         res["gen_s"] = time.time() - t0
         dg = pbng.to_device(g, dev)
         P = 200
-        pbng.tip_decompose(dg, "U", P=P)
-        t, (_, st) = timed(lambda: pbng.tip_decompose(dg, "U", P=P, with_stats=True), dev, flush)
-        res.update({"m": g.m, "P": P, "ms": t, "wedges_per_s": (st["wedges_count"] + st["wedges_cd"] + st["wedges_fd"]) / (t / 1e3),
+        pbng.tip_decompose(dg, "U", P=P, graph_rounds=args.graph_rounds)
+        t, (_, st) = timed(lambda: pbng.tip_decompose(dg, "U", P=P, with_stats=True, graph_rounds=args.graph_rounds),
+                           dev, flush)
+        res.update({"m": g.m, "P": P, "ms": t, "graph_rounds": args.graph_rounds, "wedges_per_s": (st["wedges_count"] + st["wedges_cd"] + st["wedges_fd"]) / (t / 1e3),
                     "stats": st})
+    elif args.workload == "tip_uniform_2k_1k_20k":
+        g = gen.make("uniform_2k_1k_20k")
+        dg = pbng.to_device(g, dev)
+        P = 8
+        kw = {"graph_rounds": args.graph_rounds}
+        for _ in range(max(args.warmup, 3)):
+            pbng.tip_decompose(dg, "U", P=P, **kw)
+        ms = []
+        for _ in range(max(args.steps, 20)):
+            t, (_, st) = timed(lambda: pbng.tip_decompose(dg, "U", P=P, with_stats=True, **kw), dev, flush)
+            ms.append(t)
+        h = gen.make("uniform_2k_1k_20k")
+        e2e = []
+        for _ in range(max(args.steps, 20)):
+            t0 = time.perf_counter()
+            pbng.tip_decompose_host(h, "U", P=P, **kw)
+            e2e.append((time.perf_counter() - t0) * 1e3)
+        res.update({"m": g.m, "P": P, "ms_median": statistics.median(ms), "e2e_host_buffers_ms_median": statistics.median(e2e),
+                    "graph_rounds": args.graph_rounds, "stats": st})
+    elif args.workload == "tip_chunglu_5m_1m_60m_learned":
+        from paper_2110_12511_gb300 import learned
+        g = gen.make("chunglu_5m_1m_60m")
+        dg = pbng.to_device(g, dev)
+        P = 200
+        mlp = learned.load()
+        out = {}
+        ref = None
+        for mode in ("estimator", "learned", "estimator", "learned"):
+            kw = {"mlp": mlp} if mode == "learned" else {}
+            t, (th, st) = timed(lambda: pbng.tip_decompose(dg, "U", P=P, with_stats=True, **kw), dev, flush)
+            th = pbng.as_u64(th)
+            if ref is None:
+                ref = th
+            assert (th == ref).all(), "learned bounds changed the tip numbers"
+            r = out.setdefault(mode, {"ms": []})
+            r["ms"].append(t)
+            r.update({k: st[k] for k in ("rounds", "parts_used", "launches", "fd_work_max", "fd_work_sum", "wedges_cd")})
+        for r in out.values():
+            r["best_ms"] = min(r["ms"])
+            r["fd_imbalance"] = r["fd_work_max"] / max(1.0, r["fd_work_sum"] / max(1, r["parts_used"]))
+        res.update({"P": P, "identical_theta": True, **out,
+                    "learned_speedup": out["estimator"]["best_ms"] / out["learned"]["best_ms"]})
     else:
         raise SystemExit(f"unknown workload {args.workload}")
     print(json.dumps(res), flush=True)
@@ -287,9 +330,12 @@ def main():
     ap.add_argument("--P", type=int, default=150)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer run (profiling)")
-    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="default: the bench line; others: tip_uniform_2k_1k_20k, wing_chunglu_500k_100k_5m_planted, "
+                         "tip_batch_4096, tip_chunglu_5m_1m_60m, tip_chunglu_5m_1m_60m_learned")
     ap.add_argument("--batch", type=int, default=4096)
-    ap.add_argument("--graph-rounds", action="store_true", help="coarse rounds as a CUDA graph with a device loop")
+    ap.add_argument("--host-rounds", dest="graph_rounds", action="store_false",
+                    help="drive the coarse rounds from the host (default: one CUDA graph per range, device loop)")
     ap.add_argument("--no-recount", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the coarse-peel schedule per side with the autotuner before timing (not timed)")
@@ -368,14 +414,26 @@ def main():
     wedges_step = tip_wedges(stats[0][0]) + tip_wedges(stats[0][1])
     value = ws * wedges_step * args.steps / (ms_max / 1000.0)
 
-    # ---- kernel roofline: dominant kernel group over the timed steps
+    # ---- kernel roofline: dominant kernel group, CUDA events around every
+    # launch of a group.  Graph-captured rounds run the same peel kernels
+    # inside a device loop where no per-launch event can be placed, so the
+    # roofline then comes from extra steps with host-driven rounds (untimed
+    # for the headline value).
+    roof_stats = stats
+    if args.graph_rounds:
+        host_kws = {s: dict(kws[s], graph_rounds=False) for s in kws}
+        roof_stats = []
+        for _ in range(min(args.steps, 2)):
+            flush.zero_()
+            roof_stats.append((pbng.tip_decompose(dg, "U", P=args.P, with_stats=True, **host_kws["U"])[1],
+                               pbng.tip_decompose(dg, "V", P=args.P, with_stats=True, **host_kws["V"])[1]))
     groups = {"count": ("ns_k_count", "bytes_count", "n_k_count"), "peel": ("ns_k_peel", "bytes_peel", "n_k_peel"),
               "fd": ("ns_k_fd", "bytes_fd", "n_k_fd")}
     agg = {}
     for k, (tn, bn, nn) in groups.items():
-        ns = sum(s[tn] for st in stats for s in st)
-        by = sum(s[bn] for st in stats for s in st)
-        nl = sum(s[nn] for st in stats for s in st)
+        ns = sum(s[tn] for st in roof_stats for s in st)
+        by = sum(s[bn] for st in roof_stats for s in st)
+        nl = sum(s[nn] for st in roof_stats for s in st)
         agg[k] = (ns, by, nl)
     dom = max(agg, key=lambda k: agg[k][0])
     ns, by, nl = agg[dom]
@@ -384,6 +442,7 @@ def main():
     tr = ncu_traffic(dom)
     roofline = {"bound": "hbm", "kernel_group": dom, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": tr,
+                "timing": "CUDA events per launch" + (", host-driven rounds (same kernels)" if args.graph_rounds else ""),
                 "launches": nl, "ms_per_launch": ns / 1e6 / max(nl, 1),
                 "groups": {k: {"ms": v[0] / 1e6, "GB": v[1] / 1e9, "launches": v[2],
                                "GBps": (v[1] / v[0] if v[0] else 0.0)} for k, v in agg.items()}}

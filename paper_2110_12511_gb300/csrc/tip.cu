@@ -44,6 +44,7 @@ constexpr uint32_t P_CHUNK = 2 * PB_CAP;         // block-class dense counters (
 constexpr uint32_t BK_SHIFT_MIN = 14;            // target buckets are at least P_CHUNK ids wide
 constexpr uint64_t BOFF_BUDGET = 2ull << 30;     // most bytes of bucket offsets
 constexpr uint64_t ITEM_W = 32768;               // wedges per block-class work item (at least)
+constexpr double LEARNED_JUDGE = 2.0;            // a learned range may hold 2x the estimator's target work
 constexpr int PB_PER_SM = 3;                     // resident blocks per SM (shared memory bound)
 constexpr uint32_t P_DENSE = 16384;              // fine phase: dense shared counters when |X_p| <= this
 constexpr int PBT = 512, PWT = 256;
@@ -744,6 +745,15 @@ __global__ void k_compact_list(const uint32_t *in, uint32_t n, const uint8_t *st
   }
 }
 
+// work proxy of the remaining vertices with support below a bound
+__global__ void k_work_below(const uint32_t *alist, uint32_t na, const ull *sup, const ull *wl, ull bound, ull *out) {
+  ull s = 0;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < na; j += (size_t)gridDim.x * blockDim.x)
+    if (sup[alist[j]] < bound) s += wl[j];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
 // key range of the remaining vertices only (no work proxy)
 __global__ void k_keyrange(const uint32_t *alist, uint32_t na, const ull *sup, RangeState *rs) {
   ull mn = ~0ull, mx = 0;
@@ -1398,17 +1408,19 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     bool last = pi + 1 >= P;
     CK(cudaMemsetAsync(rs, 0, sizeof(RangeState), a.st));
     set_u64(a, (uint64_t *)&rs->kmin, ~0ull);
-    // the work proxy is only needed when find_range will run
+    // the work proxy is only needed when find_range will run, or when the
+    // estimator judges a learned bound
+    const bool judged = prm.bounds_mode == PBNG_BOUNDS_LEARNED && !last;
     bool given = last || (explicit_bounds && pi < n_bounds);
     ull hk[3];
-    if (given) {
+    if (given && !judged) {
       k_keyrange<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, sup, rs);
       CK_LAUNCH();
       CK(cudaMemcpyAsync(hk, &rs->kmin, sizeof(hk), cudaMemcpyDeviceToHost, a.st));
       CK(cudaStreamSynchronize(a.st));
       given = last || bounds[pi] > hk[0];
     }
-    if (!given) {
+    if (!given || judged) {
       CK(cudaMemsetAsync(rs, 0, sizeof(RangeState), a.st));
       set_u64(a, (uint64_t *)&rs->kmin, ~0ull);
       k_weights<<<grid_for((size_t)na * 32, T, cap), T, 0, a.st>>>(alist, na, p_off, p_adj, o_len, sup, wl, rs);
@@ -1434,6 +1446,20 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       use_est = false;
     }
     uint64_t init_est = 0;
+    if (!use_est && judged && wsum > 0) {
+      // the plain estimator judges a learned bound: its range may hold at
+      // most LEARNED_JUDGE times the estimator's target work, else the
+      // estimator's own bound is used
+      double t = (double)wsum * scale / (double)(P - pi);
+      ull *d = a.zeros<ull>(1), wb = 0;
+      k_work_below<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, sup, wl, thi, d);
+      CK_LAUNCH();
+      CK(cudaMemcpyAsync(&wb, d, 8, cudaMemcpyDeviceToHost, a.st));
+      CK(cudaStreamSynchronize(a.st));
+      a.free(d);
+      if ((double)wb > LEARNED_JUDGE * std::max(t, 1.0)) use_est = true;
+      else init_est = wb;
+    }
     if (use_est) {
       if (wsum == 0 || kmin == kmax) {
         thi = kmin + 1;

@@ -120,9 +120,8 @@ def test_learned_bounds_give_identical_tip_numbers(pbng, name):
 def test_learned_bounds_gain_on_heldout_graph(pbng):
     """What the trained proposer gains over find_range on a graph from its
     training distribution that it never saw (seed 1000): identical tip
-    numbers, no per-range estimation (fewer launches), and not slower.
-    (On the 60M-edge graph, 3x larger than any training graph, it is slower;
-    find_range therefore stays the default.)"""
+    numbers and not slower.  (The estimator judges every learned bound and
+    replaces one whose range would hold more than twice its target work.)"""
     import time
     import torch
     from paper_2110_12511_gb300 import learned, train_bounds
@@ -143,6 +142,5 @@ def test_learned_bounds_gain_on_heldout_graph(pbng):
     t_est, (th_est, st_est) = run(None)
     t_lrn, (th_lrn, st_lrn) = run(mlp)
     assert np.array_equal(pbng.as_u64(th_est), pbng.as_u64(th_lrn))
-    assert st_lrn["launches"] < st_est["launches"]
     print(f"learned / find_range time: {t_lrn:.4f} / {t_est:.4f} s = {t_est / t_lrn:.2f}x")
     assert t_lrn <= 1.1 * t_est
