@@ -51,12 +51,20 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_sources_sha():
+# the sources each kernel group is compiled from
+GROUP_SOURCES = {"peel": ("tip.cu", "wedge.cuh", "fdwin.cuh", "internal.cuh"),
+                 "fd": ("tip.cu", "wedge.cuh", "fdwin.cuh", "internal.cuh"),
+                 "count": ("count.cu", "wedge.cuh", "internal.cuh")}
+
+
+def kernel_sources_sha(group):
+    """Hash of the sources of one kernel group (a stored traffic figure is
+    used only while they are unchanged)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2110_12511_gb300", "csrc")
-    for n in sorted(os.listdir(d)):
-        if n.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, n), "rb").read())
+    for n in GROUP_SOURCES[group]:
+        h.update(open(os.path.join(d, n), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "pbng.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -66,7 +74,7 @@ def ncu_traffic(group):
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    sha = kernel_sources_sha()
+    sha = kernel_sources_sha(group)
     for line in open(p):
         f = line.split()
         if len(f) >= 4 and not line.startswith("#") and f[0] == WORKLOAD and f[1] == group and f[2] == sha:
@@ -133,6 +141,21 @@ def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x, ws, device):
+    """Largest value of a host float over all ranks (all_reduce MAX); x when ws == 1."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, seconds_max):
+    """Units all ranks processed (each rank the same replica workload) per second of the slowest."""
+    return ws * units_per_rank / seconds_max
 
 
 def tip_wedges(st):
@@ -406,13 +429,9 @@ def main():
     torch.cuda.synchronize(dev)
     if ws > 1:
         dist.barrier()
-    ms_total = sum(times)
-    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(sum(times), ws, dev)
     wedges_step = tip_wedges(stats[0][0]) + tip_wedges(stats[0][1])
-    value = ws * wedges_step * args.steps / (ms_max / 1000.0)
+    value = whole_job_rate(wedges_step * args.steps, ws, ms_max / 1000.0)
 
     # ---- kernel roofline: dominant kernel group, CUDA events around every
     # launch of a group.  Graph-captured rounds run the same peel kernels
@@ -469,10 +488,8 @@ def main():
         _, sv = pbng.tip_decompose_host(hg, "V", P=args.P, with_stats=True, **kws["V"])
         e2e_t.append(time.perf_counter() - t0)
         e2e_w += tip_wedges(su) + tip_wedges(sv)
-    tt = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_value = ws * e2e_w / float(tt.item()) if e2e_t else None
+    e2e_max = max_over_ranks(sum(e2e_t), ws, dev)
+    e2e_value = whole_job_rate(e2e_w, ws, e2e_max) if e2e_t else None
     h2d = 2 * ((g.nu + 1) * 8 + g.m * 4)
     d2h = (g.nu + g.nv) * 8
 
