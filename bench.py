@@ -338,6 +338,27 @@ def run_extra(args):
             r["fd_imbalance"] = r["fd_work_max"] / max(1.0, r["fd_work_sum"] / max(1, r["parts_used"]))
         res.update({"P": P, "identical_theta": True, **out,
                     "learned_speedup": out["estimator"]["best_ms"] / out["learned"]["best_ms"]})
+    elif args.workload in ("tip_ablation", "tip_p_sweep"):
+        g = gen.make(WORKLOAD)
+        dg = pbng.to_device(g, dev)
+
+        def run(side, P, **kw):
+            pbng.tip_decompose(dg, side, P=P, **kw)  # warm
+            t, (_, st) = timed(lambda: pbng.tip_decompose(dg, side, P=P, with_stats=True, **kw), dev, flush)
+            return {"ms": t, "wedges_cd": st["wedges_cd"], "wedges_fd": st["wedges_fd"], "updates": st["updates"],
+                    "rounds": st["rounds"], "recounts": st["recounts"], "parts_used": st["parts_used"],
+                    "phase_ms": {k: st["ns_" + k] / 1e6 for k in ("count", "cd", "part", "fd")},
+                    "fd_work_max": st["fd_work_max"], "fd_work_sum": st["fd_work_sum"]}
+
+        if args.workload == "tip_ablation":
+            # Sec. 6 ablations: PBNG, PBNG- (no dynamic graph updates), PBNG-- (neither dynamic
+            # updates nor batched re-counting); host-driven rounds (the re-count branch)
+            variants = {"PBNG": {}, "PBNG-": {"compact": False}, "PBNG--": {"compact": False, "recount": False}}
+            for side in ("U", "V"):
+                res[side] = {name: run(side, args.P, **kw) for name, kw in variants.items()}
+        else:  # partition count sweep, both sides, default configuration
+            for side in ("U", "V"):
+                res[side] = {str(P): run(side, P) for P in (10, 50, 150, 400, 1000)}
     else:
         raise SystemExit(f"unknown workload {args.workload}")
     print(json.dumps(res), flush=True)
@@ -355,7 +376,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer run (profiling)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="default: the bench line; others: tip_uniform_2k_1k_20k, wing_chunglu_500k_100k_5m_planted, "
-                         "tip_batch_4096, tip_chunglu_5m_1m_60m, tip_chunglu_5m_1m_60m_learned")
+                         "tip_batch_4096, tip_chunglu_5m_1m_60m, tip_chunglu_5m_1m_60m_learned, tip_ablation, "
+                         "tip_p_sweep")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--host-rounds", dest="graph_rounds", action="store_false",
                     help="drive the coarse rounds from the host (default: one CUDA graph per range, device loop)")
