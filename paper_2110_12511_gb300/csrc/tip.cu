@@ -44,7 +44,7 @@ constexpr uint32_t P_CHUNK = 2 * PB_CAP;         // block-class dense counters (
 constexpr uint32_t BK_SHIFT_MIN = 14;            // target buckets are at least P_CHUNK ids wide
 constexpr uint64_t BOFF_BUDGET = 2ull << 30;     // most bytes of bucket offsets
 constexpr uint64_t ITEM_W = 32768;               // wedges per block-class work item (at least)
-constexpr double LEARNED_JUDGE = 2.0;            // a learned range may hold 2x the estimator's target work
+constexpr double LEARNED_VET = 2.0;              // a learned range may hold 2x the estimator's target work
 constexpr int PB_PER_SM = 3;                     // resident blocks per SM (shared memory bound)
 constexpr uint32_t P_DENSE = 16384;              // fine phase: dense shared counters when |X_p| <= this
 constexpr int PBT = 512, PWT = 256;
@@ -1409,18 +1409,18 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     CK(cudaMemsetAsync(rs, 0, sizeof(RangeState), a.st));
     set_u64(a, (uint64_t *)&rs->kmin, ~0ull);
     // the work proxy is only needed when find_range will run, or when the
-    // estimator judges a learned bound
-    const bool judged = prm.bounds_mode == PBNG_BOUNDS_LEARNED && !last;
+    // estimator vets a learned bound
+    const bool vetted = prm.bounds_mode == PBNG_BOUNDS_LEARNED && !last;
     bool given = last || (explicit_bounds && pi < n_bounds);
     ull hk[3];
-    if (given && !judged) {
+    if (given && !vetted) {
       k_keyrange<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, sup, rs);
       CK_LAUNCH();
       CK(cudaMemcpyAsync(hk, &rs->kmin, sizeof(hk), cudaMemcpyDeviceToHost, a.st));
       CK(cudaStreamSynchronize(a.st));
       given = last || bounds[pi] > hk[0];
     }
-    if (!given || judged) {
+    if (!given || vetted) {
       CK(cudaMemsetAsync(rs, 0, sizeof(RangeState), a.st));
       set_u64(a, (uint64_t *)&rs->kmin, ~0ull);
       k_weights<<<grid_for((size_t)na * 32, T, cap), T, 0, a.st>>>(alist, na, p_off, p_adj, o_len, sup, wl, rs);
@@ -1446,9 +1446,9 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       use_est = false;
     }
     uint64_t init_est = 0;
-    if (!use_est && judged && wsum > 0) {
-      // the plain estimator judges a learned bound: its range may hold at
-      // most LEARNED_JUDGE times the estimator's target work, else the
+    if (!use_est && vetted && wsum > 0) {
+      // the plain estimator vets a learned bound: its range may hold at
+      // most LEARNED_VET times the estimator's target work, else the
       // estimator's own bound is used
       double t = (double)wsum * scale / (double)(P - pi);
       ull *d = a.zeros<ull>(1), wb = 0;
@@ -1457,7 +1457,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       CK(cudaMemcpyAsync(&wb, d, 8, cudaMemcpyDeviceToHost, a.st));
       CK(cudaStreamSynchronize(a.st));
       a.free(d);
-      if ((double)wb > LEARNED_JUDGE * std::max(t, 1.0)) use_est = true;
+      if ((double)wb > LEARNED_VET * std::max(t, 1.0)) use_est = true;
       else init_est = wb;
     }
     if (use_est) {

@@ -120,7 +120,7 @@ def test_learned_bounds_give_identical_tip_numbers(pbng, name):
 def test_learned_bounds_gain_on_heldout_graph(pbng):
     """What the trained proposer gains over find_range on a graph from its
     training distribution that it never saw (seed 1000): identical tip
-    numbers and not slower.  (The estimator judges every learned bound and
+    numbers and not slower.  (The estimator vets every learned bound and
     replaces one whose range would hold more than twice its target work.)"""
     import time
     import torch
