@@ -338,6 +338,24 @@ def run_extra(args):
             r["fd_imbalance"] = r["fd_work_max"] / max(1.0, r["fd_work_sum"] / max(1, r["parts_used"]))
         res.update({"P": P, "identical_theta": True, **out,
                     "learned_speedup": out["estimator"]["best_ms"] / out["learned"]["best_ms"]})
+    elif args.workload == "tip_components":
+        # k-tips of both sides of the 1M x 200k graph at the median and the 99th
+        # percentile tip number (tip numbers from the decomposition, not timed)
+        g = gen.make(WORKLOAD)
+        dg = pbng.to_device(g, dev)
+        for side in ("U", "V"):
+            th = pbng.tip_decompose(dg, side, P=args.P)
+            thn = pbng.as_u64(th)
+            out = {}
+            for q in (50, 99):
+                k = int(np.percentile(thn, q))
+                pbng.tip_components(dg, side, th, k)
+                t, (comp, st) = timed(lambda: pbng.tip_components(dg, side, th, k, with_stats=True), dev, flush)
+                c = comp.cpu().numpy().view(np.uint32)
+                mem = c != 0xFFFFFFFF
+                out[f"p{q}"] = {"k": k, "ms": t, "members": int(mem.sum()), "tips": int(len(np.unique(c[mem]))),
+                                "wedges": st["wedges_fd"], "pairs": st["updates"]}
+            res[side] = out
     elif args.workload in ("tip_ablation", "tip_p_sweep"):
         g = gen.make(WORKLOAD)
         dg = pbng.to_device(g, dev)
@@ -377,7 +395,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="default: the bench line; others: tip_uniform_2k_1k_20k, wing_chunglu_500k_100k_5m_planted, "
                          "tip_batch_4096, tip_chunglu_5m_1m_60m, tip_chunglu_5m_1m_60m_learned, tip_ablation, "
-                         "tip_p_sweep")
+                         "tip_p_sweep, tip_components")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--host-rounds", dest="graph_rounds", action="store_false",
                     help="drive the coarse rounds from the host (default: one CUDA graph per range, device loop)")

@@ -159,6 +159,19 @@ int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, c
 int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng_side side, uint32_t P,
                              uint64_t *const *outs, const pbng_opts *opts, pbng_stats *stats);
 
+/* k-tips from tip numbers (Def. 2; the k-tip hierarchy indexed by tip numbers,
+ * Sec. 2.2).  theta: the tip numbers of `side` (as written by
+ * pbng_tip_decompose), one uint64 per vertex.  out_comp[x] receives, for
+ * every vertex with theta[x] >= k, the smallest id of its k-tip: the
+ * vertices of that side with tip number >= k, joined whenever two of them
+ * share at least two neighbours (lie in a common butterfly), split into
+ * connected components.  Vertices with theta[x] < k get 0xffffffff.  k = 0
+ * takes every vertex (a vertex in no butterfly is its own component).
+ * Pointers live where opts->mem says (device by default).  Errors as for
+ * pbng_tip_decompose; PBNG_ETIMEOUT if a union-find retry limit is hit. */
+int pbng_tip_components(const pbng_bigraph *g, pbng_side side, const uint64_t *theta, uint64_t k,
+                        uint32_t *out_comp, const pbng_opts *opts, pbng_stats *stats);
+
 /* Per-vertex butterfly counts of the U side, computed WITHOUT ANY DEVICE
  * ALLOCATION.  The paper has no counterpart: this is an access path for
  * callers that cannot allocate device memory, such as code that must stay

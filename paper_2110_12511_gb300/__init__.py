@@ -90,6 +90,8 @@ def lib():
         L.pbng_wing_decompose.restype = C
         L.pbng_tip_decompose_batch.argtypes = [G, ctypes.c_uint32, C, ctypes.c_uint32, ctypes.POINTER(P), O, S]
         L.pbng_tip_decompose_batch.restype = C
+        L.pbng_tip_components.argtypes = [G, C, P, ctypes.c_uint64, P, O, S]
+        L.pbng_tip_components.restype = C
         L.pbng_strerror.argtypes = [C]
         L.pbng_strerror.restype = ctypes.c_char_p
         L.pbng_last_error_detail.argtypes = []
@@ -324,6 +326,25 @@ def tip_decompose_batch(dgs, side="U", P=150, stream=None, with_stats=False, **k
     _check(rc, "pbng_tip_decompose_batch")
     res = [t[:(d.nu if s == SIDE_U else d.nv)] for t, d in zip(outs, dgs)]
     return (res, st.to_dict()) if with_stats else res
+
+
+def tip_components(dg: DeviceGraph, side, theta, k, stream=None, with_stats=False):
+    """k-tips from tip numbers: per vertex of `side`, the smallest id of its
+    k-tip (int32 tensor holding uint32; -1 = 0xffffffff for theta < k)."""
+    import torch
+    s = _side(side)
+    n = dg.nu if s == SIDE_U else dg.nv
+    th = theta.to(device=dg.u_off.device, dtype=torch.int64).contiguous()
+    if th.numel() < n:
+        raise ValueError("theta has fewer entries than the side has vertices")
+    out = torch.empty(max(n, 1), dtype=torch.int32, device=dg.u_off.device)
+    o = _opts(stream)
+    st = Stats()
+    g = dg.c_struct()
+    rc = lib().pbng_tip_components(ctypes.byref(g), s, th.data_ptr(), int(k), out.data_ptr(), ctypes.byref(o),
+                                   ctypes.byref(st))
+    _check(rc, "pbng_tip_components")
+    return (out[:n], st.to_dict()) if with_stats else out[:n]
 
 
 def vertex_counts_noalloc(dg: DeviceGraph, dg_t: DeviceGraph, stream=None):

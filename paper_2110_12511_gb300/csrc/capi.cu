@@ -293,6 +293,41 @@ int pbng_tip_decompose(const pbng_bigraph *g, pbng_side side, uint32_t P, uint64
   });
 }
 
+int pbng_tip_components(const pbng_bigraph *g, pbng_side side, const uint64_t *theta, uint64_t k, uint32_t *out_comp,
+                        const pbng_opts *opts, pbng_stats *stats) {
+  pbng_opts o = opts ? *opts : defaults();
+  return guarded([&] {
+    if (side != PBNG_SIDE_U && side != PBNG_SIDE_V) fail(PBNG_EINVAL, "side must be PBNG_SIDE_U or PBNG_SIDE_V");
+    check_graph(g);
+    uint32_t n = side == PBNG_SIDE_U ? g->nu : g->nv;
+    if (n && (!theta || !out_comp)) fail(PBNG_EINVAL, "null theta or out_comp");
+    init_device_pool();
+    Arena a((cudaStream_t)o.stream);
+    Timer tm(a.st);
+    pbng_bigraph d = device_graph(a, g, o.mem);
+    Graph G;
+    build_graph(a, d, false, false, G);
+    const uint64_t *th = theta;
+    uint32_t *out = out_comp;
+    if (o.mem == PBNG_MEM_HOST && n) {
+      uint64_t *t = a.alloc<uint64_t>(n);
+      CK(cudaMemcpyAsync(t, theta, (size_t)n * 8, cudaMemcpyHostToDevice, a.st));
+      th = t;
+      out = a.alloc<uint32_t>(n);
+    }
+    uint64_t wedges = 0, joins = 0;
+    tip_components(a, G, side == PBNG_SIDE_U ? 0 : 1, th, k, out, &wedges, &joins);
+    if (o.mem == PBNG_MEM_HOST && n) CK(cudaMemcpyAsync(out_comp, out, (size_t)n * 4, cudaMemcpyDeviceToHost, a.st));
+    CK(cudaStreamSynchronize(a.st));
+    if (stats) {
+      memset(stats, 0, sizeof(*stats));
+      stats->wedges_fd = wedges;  // wedges of the members' subgraph
+      stats->updates = joins;     // pairs found in a common butterfly
+      stats->ns_total = tm.ns();
+    }
+  });
+}
+
 int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, const pbng_opts *opts, pbng_stats *stats) {
   pbng_opts o = opts ? *opts : defaults();
   return guarded([&] {

@@ -169,6 +169,12 @@ struct TipParams {
 };
 void tip_decompose(Arena &a, Graph &G, int side, const TipParams &p, uint64_t *theta_out, pbng_stats *st);
 
+// ------------------------------------------------------------ k-tips
+// Component of every vertex of `side` in the k-tips (smallest member id), or
+// 0xffffffff when theta < k; theta on the device.  Optional counters.
+void tip_components(Arena &a, Graph &G, int side, const uint64_t *theta, uint64_t k, uint32_t *out, uint64_t *wedges,
+                    uint64_t *joins);
+
 // ------------------------------------------------------- learned bounds
 uint64_t bound_features(Arena &a, const uint64_t *sup, const uint32_t *p_off, uint32_t nx, float *out128);
 std::vector<uint64_t> propose_bounds(Arena &a, const float *params, uint32_t hidden, uint32_t out, const float *feat,
