@@ -159,6 +159,14 @@ int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, c
 int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng_side side, uint32_t P,
                              uint64_t *const *outs, const pbng_opts *opts, pbng_stats *stats);
 
+/* Wing numbers of many independent graphs in one call: the graphs are
+ * decomposed as their disjoint union (no butterfly crosses two graphs, so
+ * every graph's wing numbers are its own); outs[i] (m_i entries, graph i's
+ * U-CSR edge order) receives graph i's numbers (may be NULL when m_i = 0).
+ * Pointers as for pbng_tip_decompose_batch. */
+int pbng_wing_decompose_batch(const pbng_bigraph *gs, uint32_t n, uint32_t P, uint64_t *const *outs,
+                              const pbng_opts *opts, pbng_stats *stats);
+
 /* k-tips from tip numbers (Def. 2; the k-tip hierarchy indexed by tip numbers,
  * Sec. 2.2).  theta: the tip numbers of `side` (as written by
  * pbng_tip_decompose), one uint64 per vertex.  out_comp[x] receives, for

@@ -90,6 +90,8 @@ def lib():
         L.pbng_wing_decompose.restype = C
         L.pbng_tip_decompose_batch.argtypes = [G, ctypes.c_uint32, C, ctypes.c_uint32, ctypes.POINTER(P), O, S]
         L.pbng_tip_decompose_batch.restype = C
+        L.pbng_wing_decompose_batch.argtypes = [G, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(P), O, S]
+        L.pbng_wing_decompose_batch.restype = C
         L.pbng_tip_components.argtypes = [G, C, P, ctypes.c_uint64, P, O, S]
         L.pbng_tip_components.restype = C
         L.pbng_strerror.argtypes = [C]
@@ -325,6 +327,21 @@ def tip_decompose_batch(dgs, side="U", P=150, stream=None, with_stats=False, **k
     rc = lib().pbng_tip_decompose_batch(gs, n, s, int(P), ptrs, ctypes.byref(o), ctypes.byref(st))
     _check(rc, "pbng_tip_decompose_batch")
     res = [t[:(d.nu if s == SIDE_U else d.nv)] for t, d in zip(outs, dgs)]
+    return (res, st.to_dict()) if with_stats else res
+
+
+def wing_decompose_batch(dgs, P=400, stream=None, with_stats=False, **kw):
+    """Wing numbers of many independent graphs in one call (disjoint union)."""
+    import torch
+    n = len(dgs)
+    gs = (Bigraph * max(n, 1))(*[d.c_struct() for d in dgs])
+    outs = [torch.empty(max(d.m, 1), dtype=torch.int64, device=d.u_off.device) for d in dgs]
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[o.data_ptr() for o in outs])
+    o = _opts(stream, kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), keep=[])
+    st = Stats()
+    rc = lib().pbng_wing_decompose_batch(gs, n, int(P), ptrs, ctypes.byref(o), ctypes.byref(st))
+    _check(rc, "pbng_wing_decompose_batch")
+    res = [t[:d.m] for t, d in zip(outs, dgs)]
     return (res, st.to_dict()) if with_stats else res
 
 

@@ -412,6 +412,15 @@ __global__ void k_union(const BatchDesc *ds, uint32_t n, uint64_t *uoff, uint32_
   }
 }
 
+// per-edge numbers of graph gi: its edges are [e_base, e_base + m) of the union's U-CSR order
+__global__ void k_scatter_edges(const uint64_t *wing, const BatchDesc *ds, uint32_t n, uint64_t *const *outs) {
+  for (uint32_t gi = blockIdx.x; gi < n; gi += gridDim.x) {
+    BatchDesc d = ds[gi];
+    uint64_t *o = outs[gi];
+    for (uint32_t e = threadIdx.x; e < d.m; e += blockDim.x) o[e] = wing[d.e_base + e];
+  }
+}
+
 __global__ void k_scatter_out(const uint64_t *theta, const BatchDesc *ds, uint32_t n, uint64_t *const *outs, int side) {
   for (uint32_t gi = blockIdx.x; gi < n; gi += gridDim.x) {
     BatchDesc d = ds[gi];
@@ -509,6 +518,91 @@ extern "C" int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng
         uint32_t cnt = side == PBNG_SIDE_U ? gs[i].nu : gs[i].nv;
         if (cnt) CK(cudaMemcpyAsync(outs[i], douts[i], (size_t)cnt * 8, cudaMemcpyDeviceToHost, a.st));
       }
+    CK(cudaStreamSynchronize(a.st));
+    if (stats) {
+      *stats = st;
+      stats->ns_total = tm.ns();
+      ps.fill();
+    }
+  });
+}
+
+extern "C" int pbng_wing_decompose_batch(const pbng_bigraph *gs, uint32_t n, uint32_t P, uint64_t *const *outs,
+                                         const pbng_opts *opts, pbng_stats *stats) {
+  pbng_opts o = opts ? *opts : defaults();
+  return guarded([&] {
+    if (n == 0) return;
+    if (!gs || !outs) fail(PBNG_EINVAL, "null graph or output array");
+    TipParams p = tip_params(P, o);
+    init_device_pool();
+    Arena a((cudaStream_t)o.stream);
+    ProfScope ps(stats, a.st);
+    Timer tm(a.st);
+    std::vector<BatchDesc> hd(n);
+    uint64_t nu = 0, nv = 0, m = 0;
+    for (uint32_t i = 0; i < n; i++) {
+      const pbng_bigraph &g = gs[i];
+      if (!g.u_off || (g.m && (!g.u_adj || !outs[i]))) fail(PBNG_EINVAL, "graph %u: null pointer", i);
+      hd[i].nu = g.nu;
+      hd[i].nv = g.nv;
+      hd[i].m = (uint32_t)g.m;
+      hd[i].u_base = (uint32_t)nu;
+      hd[i].e_base = (uint32_t)m;
+      nu += g.nu;
+      m += g.m;
+      if (nu >= (1ull << 31) || m >= (1ull << 31)) fail(PBNG_EINVAL, "batch exceeds the size limits");
+    }
+    for (uint32_t i = 0; i < n; i++) {
+      hd[i].v_base = (uint32_t)nv;
+      nv += gs[i].nv;
+    }
+    if (nu + nv >= (1ull << 31)) fail(PBNG_EINVAL, "batch exceeds the size limits");
+    for (uint32_t i = 0; i < n; i++) {
+      if (o.mem == PBNG_MEM_HOST) {
+        uint64_t *off = a.alloc<uint64_t>((size_t)gs[i].nu + 1);
+        uint32_t *adj = a.alloc<uint32_t>(gs[i].m ? gs[i].m : 1);
+        CK(cudaMemcpyAsync(off, gs[i].u_off, ((size_t)gs[i].nu + 1) * 8, cudaMemcpyHostToDevice, a.st));
+        if (gs[i].m) CK(cudaMemcpyAsync(adj, gs[i].u_adj, gs[i].m * 4, cudaMemcpyHostToDevice, a.st));
+        hd[i].u_off = off;
+        hd[i].u_adj = adj;
+      } else {
+        hd[i].u_off = gs[i].u_off;
+        hd[i].u_adj = gs[i].u_adj;
+      }
+    }
+    BatchDesc *dd = a.alloc<BatchDesc>(n);
+    CK(cudaMemcpyAsync(dd, hd.data(), n * sizeof(BatchDesc), cudaMemcpyHostToDevice, a.st));
+    uint64_t *uoff = a.alloc<uint64_t>(nu + 1);
+    uint32_t *uadj = a.alloc<uint32_t>(m ? m : 1);
+    k_union<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(dd, n, uoff, uadj);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(uoff + nu, &m, 8, cudaMemcpyHostToDevice, a.st));
+    CK(cudaStreamSynchronize(a.st));
+    pbng_bigraph ug;
+    ug.nu = (uint32_t)nu;
+    ug.nv = (uint32_t)nv;
+    ug.m = m;
+    ug.u_off = uoff;
+    ug.u_adj = uadj;
+    check_graph(&ug);
+    Graph G;
+    build_graph(a, ug, true, true, G);
+    uint64_t *wing = a.alloc<uint64_t>(m ? m : 1);
+    pbng_stats st;
+    memset(&st, 0, sizeof(st));
+    if (m) pbng::wing_decompose(a, G, p, wing, stats ? &st : nullptr);
+    std::vector<uint64_t *> douts(n);
+    for (uint32_t i = 0; i < n; i++)
+      douts[i] = (o.mem == PBNG_MEM_HOST && gs[i].m) ? a.alloc<uint64_t>(gs[i].m) : outs[i];
+    uint64_t **dptr = a.alloc<uint64_t *>(n);
+    CK(cudaMemcpyAsync(dptr, douts.data(), n * sizeof(uint64_t *), cudaMemcpyHostToDevice, a.st));
+    if (m) {
+      k_scatter_edges<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(wing, dd, n, dptr);
+      CK_LAUNCH();
+    }
+    if (o.mem == PBNG_MEM_HOST)
+      for (uint32_t i = 0; i < n; i++)
+        if (gs[i].m) CK(cudaMemcpyAsync(outs[i], douts[i], (size_t)gs[i].m * 8, cudaMemcpyDeviceToHost, a.st));
     CK(cudaStreamSynchronize(a.st));
     if (stats) {
       *stats = st;

@@ -93,3 +93,16 @@ def test_wing_counts_match_edge_counts(pbng):
     assert np.array_equal(ce, oracle.edge_counts(g))
     w = pbng.as_u64(pbng.wing_decompose(dg, P=10))
     assert (w <= ce).all()
+
+
+def test_wing_batch_matches_oracle(pbng):
+    """Many graphs in one call: every graph's wing numbers equal the oracle's."""
+    names = list(GRAPHS)
+    gs = [GRAPHS[n] for n in names] + [gen.batch_graph(2000 + i, scale=0.02) for i in range(6)]
+    empty = gen.from_edges(3, 2, [], [])
+    gs.append(empty)
+    dgs = [pbng.to_device(g) for g in gs]
+    got = pbng.wing_decompose_batch(dgs, P=30)
+    for g, n, w in zip(gs, names + [None] * 7, got):
+        want = oracle_wing(n) if n is not None else oracle.wing(g)
+        assert np.array_equal(pbng.as_u64(w), want)
