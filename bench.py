@@ -64,7 +64,6 @@ def kernel_sources_sha(group):
     d = os.path.join(ROOT, "paper_2110_12511_gb300", "csrc")
     for n in GROUP_SOURCES[group]:
         h.update(open(os.path.join(d, n), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "pbng.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
