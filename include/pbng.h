@@ -180,6 +180,16 @@ int pbng_wing_decompose_batch(const pbng_bigraph *gs, uint32_t n, uint32_t P, ui
 int pbng_tip_components(const pbng_bigraph *g, pbng_side side, const uint64_t *theta, uint64_t k,
                         uint32_t *out_comp, const pbng_opts *opts, pbng_stats *stats);
 
+/* k-wings from wing numbers (Def. 1): theta holds the m wing numbers (U-CSR
+ * edge order, as written by pbng_wing_decompose).  out_comp[e] receives, for
+ * every edge with theta[e] >= k, the smallest edge id of its k-wing: the
+ * edges with wing number >= k, two of them joined whenever they lie in a
+ * common butterfly all of whose edges have wing number >= k, split into
+ * connected components; other edges get 0xffffffff.  Pointers and errors as
+ * for pbng_tip_components. */
+int pbng_wing_components(const pbng_bigraph *g, const uint64_t *theta, uint64_t k, uint32_t *out_comp,
+                         const pbng_opts *opts, pbng_stats *stats);
+
 /* Per-vertex butterfly counts of the U side, computed WITHOUT ANY DEVICE
  * ALLOCATION.  The paper has no counterpart: this is an access path for
  * callers that cannot allocate device memory, such as code that must stay

@@ -40,3 +40,53 @@ def tip_components(g, side, theta, k):
     np.minimum.at(smallest, lab, ids)
     out[ids] = smallest[lab].astype(np.uint32)
     return out
+
+
+def wing_components(g, theta, k):
+    """k-wings (Def. 1) from wing numbers, U-CSR edge order.  E_k = edges with
+    theta >= k; for every vertex pair (u, u') the common neighbours v with
+    (u, v) and (u', v) both in E_k are listed; a pair with two or more of them
+    forms butterflies inside E_k that hold all of those edges, so they are
+    joined (union-find); each component is labelled by its smallest edge id."""
+    theta = np.asarray(theta, dtype=np.uint64)
+    m = int(g.m)
+    out = np.full(m, NONE, dtype=np.uint32)
+    mem = theta >= np.uint64(k)
+    off = np.asarray(g.u_off, dtype=np.int64)
+    adj = np.asarray(g.u_adj, dtype=np.int64)
+    vl = [[] for _ in range(g.nv)]  # v -> [(u, e)] over E_k
+    for u in range(g.nu):
+        for e in range(off[u], off[u + 1]):
+            if mem[e]:
+                vl[adj[e]].append((u, e))
+    par = list(range(m))
+
+    def find(x):
+        while par[x] != x:
+            par[x] = par[par[x]]
+            x = par[x]
+        return x
+
+    def unite(a, b):
+        a, b = find(a), find(b)
+        if a != b:
+            par[max(a, b)] = min(a, b)
+
+    for u in range(g.nu):
+        pairs = {}
+        for e in range(off[u], off[u + 1]):
+            if not mem[e]:
+                continue
+            for u2, e2 in vl[adj[e]]:
+                if u2 > u:
+                    pairs.setdefault(u2, []).append((e, e2))
+        for lst in pairs.values():
+            if len(lst) >= 2:
+                r = lst[0][0]
+                for e, e2 in lst:
+                    unite(e, r)
+                    unite(e2, r)
+    for e in range(m):
+        if mem[e]:
+            out[e] = find(e)
+    return out

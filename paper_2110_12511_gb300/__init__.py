@@ -92,6 +92,8 @@ def lib():
         L.pbng_tip_decompose_batch.restype = C
         L.pbng_wing_decompose_batch.argtypes = [G, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(P), O, S]
         L.pbng_wing_decompose_batch.restype = C
+        L.pbng_wing_components.argtypes = [G, P, ctypes.c_uint64, P, O, S]
+        L.pbng_wing_components.restype = C
         L.pbng_tip_components.argtypes = [G, C, P, ctypes.c_uint64, P, O, S]
         L.pbng_tip_components.restype = C
         L.pbng_strerror.argtypes = [C]
@@ -362,6 +364,23 @@ def tip_components(dg: DeviceGraph, side, theta, k, stream=None, with_stats=Fals
                                    ctypes.byref(st))
     _check(rc, "pbng_tip_components")
     return (out[:n], st.to_dict()) if with_stats else out[:n]
+
+
+def wing_components(dg: DeviceGraph, theta, k, stream=None, with_stats=False):
+    """k-wings from wing numbers: per edge, the smallest edge id of its k-wing
+    (int32 tensor holding uint32; -1 = 0xffffffff for theta < k)."""
+    import torch
+    th = theta.to(device=dg.u_off.device, dtype=torch.int64).contiguous()
+    if th.numel() < dg.m:
+        raise ValueError("theta has fewer entries than the graph has edges")
+    out = torch.empty(max(dg.m, 1), dtype=torch.int32, device=dg.u_off.device)
+    o = _opts(stream)
+    st = Stats()
+    g = dg.c_struct()
+    rc = lib().pbng_wing_components(ctypes.byref(g), th.data_ptr(), int(k), out.data_ptr(), ctypes.byref(o),
+                                    ctypes.byref(st))
+    _check(rc, "pbng_wing_components")
+    return (out[:dg.m], st.to_dict()) if with_stats else out[:dg.m]
 
 
 def vertex_counts_noalloc(dg: DeviceGraph, dg_t: DeviceGraph, stream=None):

@@ -328,6 +328,40 @@ int pbng_tip_components(const pbng_bigraph *g, pbng_side side, const uint64_t *t
   });
 }
 
+int pbng_wing_components(const pbng_bigraph *g, const uint64_t *theta, uint64_t k, uint32_t *out_comp,
+                         const pbng_opts *opts, pbng_stats *stats) {
+  pbng_opts o = opts ? *opts : defaults();
+  return guarded([&] {
+    check_graph(g);
+    uint64_t m = g->m;
+    if (m && (!theta || !out_comp)) fail(PBNG_EINVAL, "null theta or out_comp");
+    init_device_pool();
+    Arena a((cudaStream_t)o.stream);
+    Timer tm(a.st);
+    pbng_bigraph d = device_graph(a, g, o.mem);
+    Graph G;
+    build_graph(a, d, false, false, G);
+    const uint64_t *th = theta;
+    uint32_t *out = out_comp;
+    if (o.mem == PBNG_MEM_HOST && m) {
+      uint64_t *t = a.alloc<uint64_t>(m);
+      CK(cudaMemcpyAsync(t, theta, (size_t)m * 8, cudaMemcpyHostToDevice, a.st));
+      th = t;
+      out = a.alloc<uint32_t>(m);
+    }
+    uint64_t wedges = 0, joins = 0;
+    wing_components(a, G, th, k, out, &wedges, &joins);
+    if (o.mem == PBNG_MEM_HOST && m) CK(cudaMemcpyAsync(out_comp, out, (size_t)m * 4, cudaMemcpyDeviceToHost, a.st));
+    CK(cudaStreamSynchronize(a.st));
+    if (stats) {
+      memset(stats, 0, sizeof(*stats));
+      stats->wedges_fd = wedges;
+      stats->updates = joins;
+      stats->ns_total = tm.ns();
+    }
+  });
+}
+
 int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, const pbng_opts *opts, pbng_stats *stats) {
   pbng_opts o = opts ? *opts : defaults();
   return guarded([&] {

@@ -174,6 +174,10 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &p, uint64_t *t
 // 0xffffffff when theta < k; theta on the device.  Optional counters.
 void tip_components(Arena &a, Graph &G, int side, const uint64_t *theta, uint64_t k, uint32_t *out, uint64_t *wedges,
                     uint64_t *joins);
+// Component of every edge in the k-wings (smallest member edge id), or
+// 0xffffffff when theta_e < k; theta on the device.
+void wing_components(Arena &a, Graph &G, const uint64_t *theta, uint64_t k, uint32_t *out, uint64_t *wedges,
+                     uint64_t *joins);
 
 // ------------------------------------------------------- learned bounds
 uint64_t bound_features(Arena &a, const uint64_t *sup, const uint32_t *p_off, uint32_t nx, float *out128);

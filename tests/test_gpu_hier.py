@@ -71,3 +71,33 @@ def test_components_heavy_members(pbng):
     for k in (1, int(theta.max()) // 2, int(theta.max())):
         got = pbng.tip_components(dg, "U", th, k).cpu().numpy().view(np.uint32)
         assert np.array_equal(got, hier.tip_components(g, "U", theta, k)), k
+
+
+@pytest.mark.parametrize("name", ["rand_40_30", "uniform_2k_1k_20k", "chunglu_5k_1k_50k_planted"])
+def test_wing_components_match_oracle(pbng, name):
+    import torch
+    g = GRAPHS[name]
+    theta = oracle.wing(g)
+    dg = pbng.to_device(g)
+    th = torch.as_tensor(theta.view(np.int64), device="cuda")
+    levels = np.unique(theta)
+    for k in sorted({0, 1, int(levels[len(levels) // 2]), int(levels[-1]), int(levels[-1]) + 1}):
+        got = pbng.wing_components(dg, th, k).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, hier.wing_components(g, theta, k)), (name, k)
+
+
+def test_wing_components_heavy_vertex(pbng):
+    """A U vertex adjacent to every V vertex (block class)."""
+    import torch
+    rng = np.random.default_rng(8)
+    nu, nv = 400, 600
+    eu = [np.zeros(nv, np.int64), rng.integers(1, nu, size=2000)]
+    ev = [np.arange(nv), rng.integers(0, nv, size=2000)]
+    key = np.unique(np.concatenate(eu) * nv + np.concatenate(ev))
+    g = gen.from_edges(nu, nv, key // nv, key % nv)
+    theta = oracle.wing(g)
+    dg = pbng.to_device(g)
+    th = torch.as_tensor(theta.view(np.int64), device="cuda")
+    for k in (1, int(np.median(theta)), int(theta.max())):
+        got = pbng.wing_components(dg, th, k).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, hier.wing_components(g, theta, k)), k

@@ -90,3 +90,52 @@ def test_hierarchy_nests_and_members_are_never_alone():
             for c in np.unique(comp[mem]):
                 assert len(np.unique(pcomp[comp == c])) == 1
         prev = (k, comp)
+
+
+def brute_wing_components(g, theta, k):
+    """Union the four edges of every butterfly whose edges all have wing number >= k."""
+    off = np.asarray(g.u_off, dtype=np.int64)
+    eid = {}
+    for u in range(g.nu):
+        for e in range(off[u], off[u + 1]):
+            eid[(u, int(g.u_adj[e]))] = e
+    mem = {e for e in range(g.m) if int(theta[e]) >= k}
+    par = {e: e for e in mem}
+
+    def find(x):
+        while par[x] != x:
+            x = par[x]
+        return x
+
+    for u1, u2 in itertools.combinations(range(g.nu), 2):
+        for v1, v2 in itertools.combinations(range(g.nv), 2):
+            es = [eid.get((u1, v1)), eid.get((u1, v2)), eid.get((u2, v1)), eid.get((u2, v2))]
+            if all(e is not None and e in mem for e in es):
+                r = min(find(e) for e in es)
+                for e in es:
+                    par[find(e)] = r
+    out = np.full(g.m, hier.NONE, dtype=np.uint32)
+    for e in mem:
+        out[e] = find(e)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_wing_brute_force_tiny(seed):
+    g = rand_graph(8, 7, 0.5, 100 + seed)
+    theta = oracle.wing(g)
+    for k in sorted(set(int(t) for t in theta)) + [0, int(theta.max()) + 1]:
+        assert np.array_equal(hier.wing_components(g, theta, k), brute_wing_components(g, theta, k)), k
+
+
+def test_wing_complete_and_disjoint_bicliques():
+    g = gen.complete(5, 4)
+    theta = oracle.wing(g)
+    assert (theta == 4 * 3).all()  # (a - 1)(b - 1)
+    assert (hier.wing_components(g, theta, 12) == 0).all()
+    eu = [u for u in range(3) for _ in range(3)] + [u for u in range(3, 6) for _ in range(3)]
+    ev = [v for _ in range(3) for v in range(3)] + [v for _ in range(3) for v in range(3, 6)]
+    g2 = gen.from_edges(6, 6, eu, ev)
+    th2 = oracle.wing(g2)
+    comp = hier.wing_components(g2, th2, 1)
+    assert list(comp) == [0] * 9 + [9] * 9
