@@ -13,7 +13,18 @@ decomposition time of both sides.
 N > 1 (one process per GPU under torch.distributed.run): every rank
 decomposes its own replica of the graph; there is no data-path collective.
 --impl reference times the CPU oracle (sequential bottom-up peeling,
-Alg. 2) on a bounded sample of the same workload.
+Alg. 2) on a bounded sample of the same workload (the same sample whatever
+--steps is).
+
+At N = 1 the line also carries the batched/learned comparison of the
+metric, each measured with CUDA events in this process:
+  batched: 4,096 independent graphs (batch workload) in one batched call
+           vs the same graphs decomposed one call at a time;
+  learned: tip decomposition of the 5M x 1M, 60M-edge Chung-Lu graph with
+           the learned bound proposer vs the plain range estimator;
+  wing:    wing decomposition of the planted 500k x 100k graph (P = 100).
+Their inputs are generated by a process pool started before the first GPU
+call, while the main workload is timed.
 """
 from __future__ import annotations
 
@@ -38,8 +49,12 @@ WORKLOAD_DESC = ("plain GPU two-phase tip decomposition of both sides, Chung-Lu 
 # CPU-baseline sample: the same Chung-Lu recipe at 1/20 scale
 SAMPLE = dict(kind="chung_lu", nu=50000, nv=10000, m=1000000, gu=2.1, gv=2.5, dmax=5000, seed=22)
 SAMPLE_DESC = "oracle BUP tip decomposition of both sides of the same Chung-Lu recipe at 1/20 scale (|U|=50k |V|=10k m=1M)"
-SAMPLE_SMALL = dict(kind="chung_lu", nu=20000, nv=4000, m=200000, gu=2.1, gv=2.5, dmax=2000, seed=12)
-SAMPLE_SMALL_DESC = "oracle BUP tip decomposition of both sides of the same Chung-Lu recipe at 1/100 scale (|U|=20k |V|=4k m=200k)"
+# the oracle's complete tip peeling of both sides of the full graph, measured once on the
+# build host when the expected results were written (tests/golden/*.json, cpu_seconds)
+GOLDEN_SIDES = ("tip_chunglu_1m_200k_20m_U", "tip_chunglu_1m_200k_20m_V")
+BATCH_N, BATCH_SEED0 = 4096, 1000
+LEARNED_WORKLOAD, LEARNED_P = "chunglu_5m_1m_60m", 200
+WING_WORKLOAD, WING_P = "chunglu_500k_100k_5m_planted", 100
 
 
 def peaks():
@@ -162,8 +177,10 @@ def tip_wedges(st):
 
 
 def oracle_sample(spec, sides=("U", "V")):
-    """Time the oracle on a sample; returns (wedges, seconds).  The oracle's
-    tip BUP traverses sum_v d_v^2 wedges to count and the same again to peel."""
+    """Time the oracle on a sample; returns (wedges, seconds).  The wedges are
+    the ones the oracle's own loops visit, counted exactly: its 2-hop count
+    visits sum_y d_y^2 wedges (y on the other side) and its peel visits every
+    wedge of each peeled vertex once more, so 2 sum_y d_y^2 per side."""
     import bigraph_gen as gen
     import oracle
     g = gen.make(dict(spec))
@@ -184,7 +201,7 @@ def run_reference(args, ws, rank):
         return 0
     import oracle
     oracle.build()
-    spec, desc = (SAMPLE, SAMPLE_DESC) if args.steps + args.warmup <= 12 else (SAMPLE_SMALL, SAMPLE_SMALL_DESC)
+    spec, desc = SAMPLE, SAMPLE_DESC
     for _ in range(args.warmup):
         oracle_sample(spec)
     tw, tt = 0.0, 0.0
@@ -382,6 +399,104 @@ def run_extra(args):
     return 0
 
 
+def _gen_worker(job):
+    """One input of the bench, generated in a spawned worker process (no GPU)."""
+    import bigraph_gen as gen
+    kind, a, b = job
+    if kind == "batch":
+        return [gen.batch_graph(s) for s in range(a, b)]
+    return gen.make(a)
+
+
+def start_inputs(extras):
+    """Spawned pool generating the main workload and, with extras, the inputs
+    of the batched / learned / wing records (started before any GPU call)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(min(12, max(2, (os.cpu_count() or 2) - 1)))
+    jobs = {"main": pool.apply_async(_gen_worker, (("make", WORKLOAD, 0),))}
+    if extras:
+        jobs["learned"] = pool.apply_async(_gen_worker, (("make", LEARNED_WORKLOAD, 0),))
+        chunk = BATCH_N // 8
+        jobs["batch"] = [pool.apply_async(_gen_worker, (("batch", BATCH_SEED0 + i, BATCH_SEED0 + i + chunk),))
+                         for i in range(0, BATCH_N, chunk)]
+        jobs["wing"] = pool.apply_async(_gen_worker, (("make", WING_WORKLOAD, 0),))
+    return pool, jobs
+
+
+def record_batched(pbng, graphs, dev, flush, P=150):
+    """The batch workload in one batched call vs one call per graph, both with
+    graph-captured coarse rounds, CUDA events on the library's stream."""
+    import torch
+    dgs = [pbng.to_device(g, dev) for g in graphs]
+    kw = {"graph_rounds": True}
+    pbng.tip_decompose_batch(dgs, "U", P=P, **kw)
+    tb, (res, stb) = timed(lambda: pbng.tip_decompose_batch(dgs, "U", P=P, with_stats=True, **kw), dev, flush)
+    for d in dgs[:16]:
+        pbng.tip_decompose(d, "U", P=P, **kw)
+    to, outs = timed(lambda: [pbng.tip_decompose(d, "U", P=P, **kw) for d in dgs], dev, flush)
+    same = all(torch.equal(a, b) for a, b in zip(res, outs))
+    assert same, "batched and one-at-a-time tip numbers differ"
+    w = tip_wedges(stb)
+    return {"workload": f"tip decomposition (U, P={P}) of {len(graphs)} Chung-Lu graphs with planted bicliques, "
+                        "m log-uniform in 1k-200k", "graphs": len(graphs), "edges": int(sum(g.m for g in graphs)),
+            "batched_ms": tb, "one_at_a_time_ms": to, "ratio": to / tb, "identical_theta": same,
+            "batched_wedges_per_s": w / (tb / 1e3), "rounds": stb["rounds"], "parts_used": stb["parts_used"],
+            "mode": "graph-captured coarse rounds in both arms"}
+
+
+def record_learned(pbng, g, dev, flush, P=LEARNED_P):
+    """Learned bound proposer vs the plain range estimator on the 60M-edge graph."""
+    from paper_2110_12511_gb300 import learned
+    dg = pbng.to_device(g, dev)
+    mlp = learned.load(device=dev)
+    out, ref = {}, None
+    for mode in ("estimator", "learned", "estimator", "learned"):
+        kw = {"mlp": mlp} if mode == "learned" else {}
+        t, (th, st) = timed(lambda: pbng.tip_decompose(dg, "U", P=P, with_stats=True, graph_rounds=True, **kw),
+                            dev, flush)
+        th = pbng.as_u64(th)
+        if ref is None:
+            ref = th
+        assert (th == ref).all(), "learned bounds changed the tip numbers"
+        r = out.setdefault(mode, {"ms": []})
+        r["ms"].append(t)
+        r.update({k: st[k] for k in ("rounds", "parts_used", "fd_work_max", "fd_work_sum", "wedges_cd", "wedges_fd")})
+        r["phase_ms"] = {k: st["ns_" + k] / 1e6 for k in ("count", "cd", "part", "fd")}
+    for r in out.values():
+        r["best_ms"] = min(r["ms"])
+        r["fd_imbalance"] = r["fd_work_max"] / max(1.0, r["fd_work_sum"] / max(1, r["parts_used"]))
+    return {"workload": f"tip decomposition (U, P={P}) of Chung-Lu |U|=5M |V|=1M m=60M, exponents 2.1/2.3",
+            "identical_theta": True, **out, "ratio": out["estimator"]["best_ms"] / out["learned"]["best_ms"]}
+
+
+def record_wing(pbng, g, dev, flush, P=WING_P):
+    """Wing decomposition of the planted 500k x 100k graph."""
+    dg = pbng.to_device(g, dev)
+    pbng.wing_decompose(dg, P=P)
+    t, (_, st) = timed(lambda: pbng.wing_decompose(dg, P=P, with_stats=True), dev, flush)
+    return {"workload": f"wing decomposition (P={P}) of Chung-Lu |U|=500k |V|=100k m=5M, exponents 2.2/2.4, "
+                        "200 planted bicliques 20-200 x 20-200", "m": g.m, "ms": t,
+            "updates_per_s": st["updates"] / (t / 1e3), "links": st["links"], "rounds": st["rounds"],
+            "parts_used": st["parts_used"], "fd_steps_max": st["fd_part_steps_max"],
+            "phase_ms": {k: st["ns_" + k] / 1e6 for k in ("count", "cd", "part", "fd")}}
+
+
+def full_graph_oracle_seconds():
+    """The oracle's measured time for the complete tip peeling of both sides of
+    the full workload (written with the stored expected results), or None."""
+    tot, hosts = 0.0, set()
+    for name in GOLDEN_SIDES:
+        p = os.path.join(ROOT, "tests", "golden", name + ".json")
+        if not os.path.exists(p):
+            return None
+        with open(p) as f:
+            d = json.load(f)
+        tot += float(d["cpu_seconds"])
+        hosts.add(d.get("host", "x86_64"))
+    return {"seconds": tot, "host": ",".join(sorted(hosts)), "cores": 1}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,6 +516,8 @@ def main():
     ap.add_argument("--no-recount", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the coarse-peel schedule per side with the autotuner before timing (not timed)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched / learned / wing records of the line")
     args = ap.parse_args()
     ws, rank, local = dist_info()
     if args.impl == "reference":
@@ -408,9 +525,11 @@ def main():
     if args.workload != WORKLOAD:
         return run_extra(args)
 
+    extras = ws == 1 and not args.no_extras
+    pool, jobs = start_inputs(extras)  # before the first GPU call
+
     import torch
     import torch.distributed as dist
-    import bigraph_gen as gen
     import paper_2110_12511_gb300 as pbng
     from paper_2110_12511_gb300 import build as pbuild
 
@@ -424,7 +543,7 @@ def main():
         dist.barrier()
     pbng.lib()
 
-    g = gen.make(WORKLOAD)
+    g = jobs["main"].get()
     dg = pbng.to_device(g, dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
@@ -532,19 +651,37 @@ def main():
     h2d = 2 * ((g.nu + 1) * 8 + g.m * 4)
     d2h = (g.nu + g.nv) * 8
 
+    ms_step = ms_max / args.steps
+    rec = {}
+    if extras:  # the batched / learned comparison of the metric, and the wing workload
+        graphs = [x for j in jobs["batch"] for x in j.get()]
+        rec["batched"] = record_batched(pbng, graphs, dev, flush)
+        del graphs
+        rec["learned"] = record_learned(pbng, jobs["learned"].get(), dev, flush)
+        rec["wing"] = record_wing(pbng, jobs["wing"].get(), dev, flush)
+    pool.close()
+
     line = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
+            import platform
             import oracle
             oracle.build()
             w, dt = oracle_sample(SAMPLE)
             cpu = {"value": w / dt, "unit": "wedges/s", "cores": 1, "kind": "oracle", "sample": SAMPLE_DESC,
-                   "seconds": dt}
+                   "seconds": dt, "host": platform.machine(),
+                   "wedges": "the oracle's own wedge visits (2 sum_y d_y^2 per side, exact for its loops); the GPU "
+                             "line counts the wedges its own method visits"}
+            full = full_graph_oracle_seconds()
+            if full:  # like for like: the same full graph, time per decomposition of both sides
+                full["gpu_ms_per_step"] = ms_step
+                full["time_ratio"] = full["seconds"] / (ms_step / 1e3)
+                cpu["full_graph"] = full
         s0u, s0v = stats[0]
         line = {
             "metric": "tip decomposition wedges/s (both sides)", "value": value, "unit": "wedges/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic (seeded Chung-Lu generator)",
             "config": {"workload": WORKLOAD_DESC, "name": WORKLOAD, "P": args.P, "sides": "U,V",
@@ -562,6 +699,7 @@ def main():
                     "ms_per_step": 1000 * sum(e2e_t) / len(e2e_t) if e2e_t else None},
             "gpu_launches": int(sum(s["launches"] for st in stats for s in st)),
             "clocks": clk.summary(),
+            **rec,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -164,6 +164,10 @@ CONFIGS = {
     # Chung-Lu |U|=500k |V|=100k m=5M, exponents 2.2 / 2.4 + 200 planted 20..200 bicliques; wing, P=100
     "chunglu_500k_100k_5m_planted": dict(kind="chung_lu", nu=500000, nv=100000, m=5000000, gu=2.2, gv=2.4,
                                          dmax=50000, seed=3, nplant=200, plant_lo=20, plant_hi=200),
+    # the same planted recipe on a 1M-edge Chung-Lu base (all 200 bicliques kept): the
+    # oracle's wing peeling finishes it in under an hour
+    "chunglu_500k_100k_1m_planted": dict(kind="chung_lu", nu=500000, nv=100000, m=1000000, gu=2.2, gv=2.4,
+                                         dmax=50000, seed=3, nplant=200, plant_lo=20, plant_hi=200),
     # Chung-Lu |U|=5M |V|=1M m=60M, exponents 2.1 / 2.3; tip of U, P=200
     "chunglu_5m_1m_60m": dict(kind="chung_lu", nu=5000000, nv=1000000, m=60000000, gu=2.1, gv=2.3,
                               dmax=50000, seed=5),

@@ -81,8 +81,11 @@ typedef struct pbng_opts {
   uint32_t mlp_hidden, mlp_out;
   uint64_t *bounds_out;    /* optional host array receiving the upper bounds theta(2), theta(3), ...
                               actually used (the last, unbounded range is not listed) */
-  uint32_t n_bounds_out;   /* capacity of bounds_out; the count written is stats->parts_used - 1
-                              (at most this many are stored) */
+  uint32_t n_bounds_out;   /* capacity of bounds_out.  One bound is written per range that was
+                              closed by a finite bound: stats->parts_used - 1 when the last range
+                              used is the unbounded range P, stats->parts_used when a finite bound
+                              already took every remaining entity (at most this many are stored;
+                              every bound is >= 1, the rest of the array is left as it was) */
   uint32_t bucket_shift;   /* tip: the coarse peel cuts the peeled side's ids into buckets of
                               2^bucket_shift ids (at most 512 buckets); 0 (default) = automatic
                               (15, raised when needed), else 14..30; results are identical */
@@ -91,6 +94,10 @@ typedef struct pbng_opts {
      default 512), by a 256-thread group when W <= group_max_w (warp_max_w..2048, default 2048),
      else by blocks, one per item of at least item_w wedges (>= 4096, default 32768) */
   uint32_t warp_max_w, group_max_w, item_w;
+  uint32_t fd_cluster_min;  /* fine phase: a partition with at least this many entities (wing: edges,
+                               tip: vertices) is peeled by a cluster of thread blocks sharing its
+                               step state instead of one block; 0 = default (32768), 0xffffffff =
+                               never; results are identical */
 } pbng_opts;
 
 typedef struct pbng_stats {
@@ -155,7 +162,11 @@ int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, c
  * sharing every launch, coarse round and fine-phase work queue.  outs[i]
  * receives the tip numbers of graph i's peeled side.  With PBNG_MEM_DEVICE
  * every gs[i] pointer and outs[i] is a device pointer; gs and outs
- * themselves are host arrays. */
+ * themselves are host arrays.  Every graph's own CSR is checked first (the
+ * conventions above, with graph i's own nv and m); a malformed graph fails
+ * the call with PBNG_EINVAL and pbng_last_error_detail() names its index.
+ * opts->bounds_out receives the bounds used for the union, and
+ * stats->ns_setup the time to build the union's internal graph. */
 int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng_side side, uint32_t P,
                              uint64_t *const *outs, const pbng_opts *opts, pbng_stats *stats);
 
@@ -163,7 +174,8 @@ int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng_side side,
  * decomposed as their disjoint union (no butterfly crosses two graphs, so
  * every graph's wing numbers are its own); outs[i] (m_i entries, graph i's
  * U-CSR edge order) receives graph i's numbers (may be NULL when m_i = 0).
- * Pointers as for pbng_tip_decompose_batch. */
+ * Pointers, per-graph checks, bounds_out and ns_setup as for
+ * pbng_tip_decompose_batch. */
 int pbng_wing_decompose_batch(const pbng_bigraph *gs, uint32_t n, uint32_t P, uint64_t *const *outs,
                               const pbng_opts *opts, pbng_stats *stats);
 
@@ -217,6 +229,30 @@ int pbng_wing_components(const pbng_bigraph *g, const uint64_t *theta, uint64_t 
 int pbng_vertex_counts_noalloc(uint32_t nu, uint32_t nv, uint64_t m, const uint64_t *u_off,
                                const uint32_t *u_adj, const uint64_t *v_off, const uint32_t *v_adj,
                                uint64_t *out_u, void *stream);
+
+/* Partition bounds of the coarse phase (Sec. 3.1.3, find_range with
+ * adaptive targets; Sec. 4.1 Th. 2: any strictly increasing bounds give the
+ * same tip numbers, so bounds only change speed).  Runs the counting and
+ * coarse phase of pbng_tip_decompose on `side` with the same options
+ * (opts->bounds_mode: the estimator, or the learned proposer of
+ * opts->mlp_params judged by the estimator as in pbng_tip_decompose, or
+ * explicit bounds) and stops before the fine phase.  out_bounds (host array
+ * of P+1 entries) receives theta(1) = 0, then the upper bound theta(i+1) of
+ * every range used, then UINT64_MAX (theta(P+1) = +infinity, and every range
+ * not needed).  Feeding out_bounds[1..] back as explicit bounds reproduces
+ * the same ranges. */
+int pbng_propose_bounds(const pbng_bigraph *g, pbng_side side, uint32_t P, uint64_t *out_bounds,
+                        const pbng_opts *opts);
+
+/* BE-Index sums (Sec. 2.3, Property 1 and Property 2): builds the
+ * Bloom-Edge-Index used by pbng_wing_decompose and reports, for every edge
+ * e, out_e[e] = sum over the maximal priority blooms B containing e of
+ * (k_B - 1) (m entries, edge-id order; equals the butterfly count of e), and
+ * *out_total (host) = sum over all blooms of C(k_B, 2) (equals the number of
+ * butterflies of the graph).  stats->links and stats->blooms give the
+ * index's size.  Pointers as for pbng_wing_decompose. */
+int pbng_be_index_sums(const pbng_bigraph *g, uint64_t *out_e, uint64_t *out_total, const pbng_opts *opts,
+                       pbng_stats *stats);
 
 /* Features of the learned bound proposer (no counterpart in the paper's
  * method; the bounds it feeds only change speed, Sec. 4.1 Th. 2): out[0..63]

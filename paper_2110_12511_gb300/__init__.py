@@ -39,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("mlp_params", ctypes.c_void_p), ("mlp_hidden", ctypes.c_uint32), ("mlp_out", ctypes.c_uint32),
                 ("bounds_out", ctypes.c_void_p), ("n_bounds_out", ctypes.c_uint32),
                 ("bucket_shift", ctypes.c_uint32), ("warp_max_w", ctypes.c_uint32),
-                ("group_max_w", ctypes.c_uint32), ("item_w", ctypes.c_uint32)]
+                ("group_max_w", ctypes.c_uint32), ("item_w", ctypes.c_uint32), ("fd_cluster_min", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -111,6 +111,10 @@ def lib():
         L.pbng_mlp_adam.argtypes = [P, P, P, P, ctypes.c_uint64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_uint32, P]
         L.pbng_mlp_adam.restype = C
+        L.pbng_propose_bounds.argtypes = [G, C, ctypes.c_uint32, P, O]
+        L.pbng_propose_bounds.restype = C
+        L.pbng_be_index_sums.argtypes = [G, P, P, O, S]
+        L.pbng_be_index_sums.restype = C
         L.pbng_vertex_counts_noalloc.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, P, P, P, P, P, P]
         L.pbng_vertex_counts_noalloc.restype = C
         _lib = L
@@ -152,7 +156,7 @@ def to_device(g, device="cuda") -> DeviceGraph:
     return DeviceGraph(int(g.nu), int(g.nv), off, adj)
 
 
-SCHEDULE_KEYS = ("bucket_shift", "warp_max_w", "group_max_w", "item_w")
+SCHEDULE_KEYS = ("bucket_shift", "warp_max_w", "group_max_w", "item_w", "fd_cluster_min")
 
 
 def _opts(stream=None, bounds=None, recount=True, compact=True, mem=MEM_DEVICE, graph_rounds=False, keep=None,
@@ -240,6 +244,34 @@ def tip_decompose(dg: DeviceGraph, side="U", P=150, bounds=None, recount=True, c
     return (out[:n], st.to_dict()) if with_stats else out[:n]
 
 
+def propose_bounds(dg: DeviceGraph, side="U", P=150, mlp=None, bounds=None, stream=None, **kw):
+    """The P+1 coarse-phase bounds theta(1..P+1) (numpy uint64; unused ranges
+    and theta(P+1) are 2^64-1) the estimator, or the learned proposer when
+    ``mlp`` is given, would use (Sec. 3.1.3)."""
+    out = np.zeros(int(P) + 1, dtype=np.uint64)
+    keep = []
+    o = _opts(stream, bounds, kw.get("recount", True), kw.get("compact", True), keep=keep, mlp=mlp,
+              graph_rounds=kw.get("graph_rounds", False), schedule=kw.get("schedule"))
+    g = dg.c_struct()
+    _check(lib().pbng_propose_bounds(ctypes.byref(g), _side(side), int(P), out.ctypes.data, ctypes.byref(o)),
+           "pbng_propose_bounds")
+    return out
+
+
+def be_index_sums(dg: DeviceGraph, stream=None, with_stats=False):
+    """(per-edge sum over its blooms of k_B - 1, sum over blooms of C(k_B, 2)) of the BE-Index."""
+    import torch
+    out = torch.empty(max(dg.m, 1), dtype=torch.int64, device=dg.u_off.device)
+    tot = ctypes.c_uint64(0)
+    o = _opts(stream)
+    st = Stats()
+    g = dg.c_struct()
+    _check(lib().pbng_be_index_sums(ctypes.byref(g), out.data_ptr(), ctypes.byref(tot), ctypes.byref(o),
+                                    ctypes.byref(st)), "pbng_be_index_sums")
+    res = (out[:dg.m], int(tot.value))
+    return (res, st.to_dict()) if with_stats else res
+
+
 def bound_features(dg: DeviceGraph, side="U", stream=None):
     """128 histogram features of the learned bound proposer (float32 tensor)."""
     import torch
@@ -300,12 +332,13 @@ def tip_decompose_host(g, side="U", P=150, with_stats=False, **kw):
     return (out[:n], st.to_dict()) if with_stats else out[:n]
 
 
-def wing_decompose(dg: DeviceGraph, P=400, bounds=None, recount=True, compact=True, stream=None, with_stats=False):
+def wing_decompose(dg: DeviceGraph, P=400, bounds=None, recount=True, compact=True, stream=None, with_stats=False,
+                   schedule=None, bounds_out=None):
     """Wing numbers of every edge (BE-Index PBNG, Sec. 3.3)."""
     import torch
     out = torch.empty(max(dg.m, 1), dtype=torch.int64, device=dg.u_off.device)
     keep = []
-    o = _opts(stream, bounds, recount, compact, keep=keep)
+    o = _opts(stream, bounds, recount, compact, keep=keep, schedule=schedule, bounds_out=bounds_out)
     st = Stats()
     g = dg.c_struct()
     rc = lib().pbng_wing_decompose(ctypes.byref(g), int(P), out.data_ptr(), ctypes.byref(o), ctypes.byref(st))
@@ -324,7 +357,7 @@ def tip_decompose_batch(dgs, side="U", P=150, stream=None, with_stats=False, **k
     keep = []
     o = _opts(stream, kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), keep=keep,
               graph_rounds=kw.get("graph_rounds", False), bucket_shift=kw.get("bucket_shift", 0),
-              schedule=kw.get("schedule"))
+              schedule=kw.get("schedule"), bounds_out=kw.get("bounds_out"))
     st = Stats()
     rc = lib().pbng_tip_decompose_batch(gs, n, s, int(P), ptrs, ctypes.byref(o), ctypes.byref(st))
     _check(rc, "pbng_tip_decompose_batch")
@@ -339,11 +372,51 @@ def wing_decompose_batch(dgs, P=400, stream=None, with_stats=False, **kw):
     gs = (Bigraph * max(n, 1))(*[d.c_struct() for d in dgs])
     outs = [torch.empty(max(d.m, 1), dtype=torch.int64, device=d.u_off.device) for d in dgs]
     ptrs = (ctypes.c_void_p * max(n, 1))(*[o.data_ptr() for o in outs])
-    o = _opts(stream, kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), keep=[])
+    o = _opts(stream, kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), keep=[],
+              bounds_out=kw.get("bounds_out"))
     st = Stats()
     rc = lib().pbng_wing_decompose_batch(gs, n, int(P), ptrs, ctypes.byref(o), ctypes.byref(st))
     _check(rc, "pbng_wing_decompose_batch")
     res = [t[:d.m] for t, d in zip(outs, dgs)]
+    return (res, st.to_dict()) if with_stats else res
+
+
+def _host_structs(graphs):
+    keep, structs = [], []
+    for g in graphs:
+        off = np.ascontiguousarray(g.u_off, dtype=np.uint64)
+        adj = np.ascontiguousarray(g.u_adj, dtype=np.uint32)
+        keep += [off, adj]
+        structs.append(Bigraph(int(g.nu), int(g.nv), adj.size, off.ctypes.data, adj.ctypes.data if adj.size else 0))
+    return keep, (Bigraph * max(len(graphs), 1))(*structs)
+
+
+def tip_decompose_batch_host(graphs, side="U", P=150, with_stats=False, **kw):
+    """Batch tip numbers with host input and output buffers (the library copies)."""
+    s = _side(side)
+    keep, gs = _host_structs(graphs)
+    outs = [np.zeros(max(g.nu if s == SIDE_U else g.nv, 1), dtype=np.uint64) for g in graphs]
+    ptrs = (ctypes.c_void_p * max(len(graphs), 1))(*[o.ctypes.data for o in outs])
+    o = _opts(kw.get("stream"), kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), mem=MEM_HOST,
+              keep=keep, graph_rounds=kw.get("graph_rounds", False), bounds_out=kw.get("bounds_out"))
+    st = Stats()
+    _check(lib().pbng_tip_decompose_batch(gs, len(graphs), s, int(P), ptrs, ctypes.byref(o), ctypes.byref(st)),
+           "pbng_tip_decompose_batch")
+    res = [t[:(g.nu if s == SIDE_U else g.nv)] for t, g in zip(outs, graphs)]
+    return (res, st.to_dict()) if with_stats else res
+
+
+def wing_decompose_batch_host(graphs, P=400, with_stats=False, **kw):
+    """Batch wing numbers with host buffers; an edgeless graph gets a NULL output."""
+    keep, gs = _host_structs(graphs)
+    outs = [np.zeros(g.m, dtype=np.uint64) if g.m else None for g in graphs]
+    ptrs = (ctypes.c_void_p * max(len(graphs), 1))(*[o.ctypes.data if o is not None else None for o in outs])
+    o = _opts(kw.get("stream"), kw.get("bounds"), kw.get("recount", True), kw.get("compact", True), mem=MEM_HOST,
+              keep=keep, bounds_out=kw.get("bounds_out"))
+    st = Stats()
+    _check(lib().pbng_wing_decompose_batch(gs, len(graphs), int(P), ptrs, ctypes.byref(o), ctypes.byref(st)),
+           "pbng_wing_decompose_batch")
+    res = [t if t is not None else np.zeros(0, dtype=np.uint64) for t in outs]
     return (res, st.to_dict()) if with_stats else res
 
 

@@ -47,11 +47,6 @@ void check_graph(const pbng_bigraph *g) {
 // Device view of the caller's graph: copies host arrays when mem == HOST.
 pbng_bigraph device_graph(Arena &a, const pbng_bigraph *g, int mem) {
   check_graph(g);
-  if (!g) fail(PBNG_EINVAL, "null graph");
-  if (!g->u_off) fail(PBNG_EINVAL, "null u_off");
-  if (g->m && !g->u_adj) fail(PBNG_EINVAL, "null u_adj with m > 0");
-  if ((uint64_t)g->nu + g->nv >= (1ull << 31) || g->m >= (1ull << 31))
-    fail(PBNG_EINVAL, "graph exceeds the size limits (nu+nv < 2^31, m < 2^31)");
   pbng_bigraph d = *g;
   if (mem == PBNG_MEM_HOST) {
     uint64_t *off = a.alloc<uint64_t>((size_t)g->nu + 1);
@@ -116,6 +111,7 @@ TipParams tip_params(uint32_t P, const pbng_opts &o) {
     p.group_max_w = gm;
     p.item_w = o.item_w;
   }
+  p.fd_cluster_min = o.fd_cluster_min ? o.fd_cluster_min : 32768u;
   p.timeout_ns = o.timeout_ns ? o.timeout_ns : 10000000000ull;
   p.mlp_params = o.mlp_params;
   p.mlp_hidden = o.mlp_hidden;
@@ -397,6 +393,59 @@ int pbng_wing_decompose(const pbng_bigraph *g, uint32_t P, uint64_t *out_wing, c
   });
 }
 
+int pbng_be_index_sums(const pbng_bigraph *g, uint64_t *out_e, uint64_t *out_total, const pbng_opts *opts,
+                       pbng_stats *stats) {
+  pbng_opts o = opts ? *opts : defaults();
+  return guarded([&] {
+    if (!out_total) fail(PBNG_EINVAL, "null out_total");
+    if (!out_e && g && g->m) fail(PBNG_EINVAL, "null out_e");
+    check_graph(g);
+    init_device_pool();
+    Arena a((cudaStream_t)o.stream);
+    Timer tm(a.st);
+    pbng_bigraph d = device_graph(a, g, o.mem);
+    Graph G;
+    build_graph(a, d, true, true, G);
+    OutBuf out;
+    out.init(a, out_e, G.m, o.mem);
+    pbng_stats st;
+    memset(&st, 0, sizeof(st));
+    uint64_t total = 0;
+    be_index_sums(a, G, out.dev, &total, &st);
+    out.finish(a);
+    CK(cudaStreamSynchronize(a.st));
+    *out_total = total;
+    if (stats) {
+      *stats = st;
+      stats->ns_total = tm.ns();
+    }
+  });
+}
+
+int pbng_propose_bounds(const pbng_bigraph *g, pbng_side side, uint32_t P, uint64_t *out_bounds,
+                        const pbng_opts *opts) {
+  pbng_opts o = opts ? *opts : defaults();
+  return guarded([&] {
+    if (side != PBNG_SIDE_U && side != PBNG_SIDE_V) fail(PBNG_EINVAL, "side must be PBNG_SIDE_U or PBNG_SIDE_V");
+    if (!out_bounds) fail(PBNG_EINVAL, "null out_bounds");
+    TipParams p = tip_params(P, o);
+    check_graph(g);
+    init_device_pool();
+    Arena a((cudaStream_t)o.stream);
+    pbng_bigraph d = device_graph(a, g, o.mem);
+    Graph G;
+    build_graph(a, d, true, false, G);
+    std::vector<uint64_t> used;
+    p.bounds_used = &used;
+    p.coarse_only = true;
+    tip_decompose(a, G, side == PBNG_SIDE_U ? 0 : 1, p, nullptr, nullptr);
+    CK(cudaStreamSynchronize(a.st));
+    // theta(1) = 0, the bounds of the ranges used, then +inf (UINT64_MAX)
+    out_bounds[0] = 0;
+    for (uint32_t i = 1; i <= P; i++) out_bounds[i] = i - 1 < used.size() ? used[i - 1] : ~0ull;
+  });
+}
+
 int pbng_bound_features(const pbng_bigraph *g, pbng_side side, float *out, const pbng_opts *opts) {
   pbng_opts o = opts ? *opts : defaults();
   return guarded([&] {
@@ -437,6 +486,43 @@ struct BatchDesc {
   uint32_t e_base;          // offset of this graph's edges in the union
 };
 
+enum { BERR_OFFSETS = 1, BERR_RANGE = 2, BERR_ORDER = 4 };
+
+// One block per graph, one warp per row: each graph's own CSR must be valid
+// on its own (u_off[0] = 0, u_off[nu] = m, non-decreasing offsets, ids below
+// its own nv, rows strictly increasing).  The union would otherwise shift a
+// bad id or offset into a neighbouring graph.  Records the smallest failing
+// graph index and the kinds of failure.  Offsets are checked before any
+// neighbour id of their row is read.
+__global__ void k_batch_validate(const BatchDesc *ds, uint32_t n, unsigned *bad_graph, unsigned *flags) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (uint32_t gi = blockIdx.x; gi < n; gi += gridDim.x) {
+    BatchDesc d = ds[gi];
+    unsigned bad = 0;
+    for (uint32_t u = warp; u <= d.nu; u += nwarps) {
+      uint64_t b = d.u_off[u];
+      if (u == d.nu) {
+        if (b != d.m) bad |= BERR_OFFSETS;
+        continue;
+      }
+      uint64_t e = d.u_off[u + 1];
+      if (b > e || e > d.m || (u == 0 && b != 0)) {
+        bad |= BERR_OFFSETS;
+        continue;
+      }
+      for (uint64_t i = b + lane; i < e; i += 32) {
+        uint32_t x = d.u_adj[i];
+        if (x >= d.nv) bad |= BERR_RANGE;
+        if (i + 1 < e && d.u_adj[i + 1] <= x) bad |= BERR_ORDER;
+      }
+    }
+    if (bad) {
+      atomicMin(bad_graph, gi);
+      atomicOr(flags, bad);
+    }
+  }
+}
+
 // one block per graph: union offsets and neighbour ids shifted into place
 __global__ void k_union(const BatchDesc *ds, uint32_t n, uint64_t *uoff, uint32_t *uadj) {
   for (uint32_t gi = blockIdx.x; gi < n; gi += gridDim.x) {
@@ -463,6 +549,83 @@ __global__ void k_scatter_out(const uint64_t *theta, const BatchDesc *ds, uint32
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) o[i] = theta[base + i];
   }
 }
+
+// The disjoint union of a batch of graphs on the device (shared by both
+// batch calls): host checks, copies of host graphs, the per-graph CSR check,
+// then the union's U-side CSR (graph i's vertices and edges shifted by the
+// sizes of graphs 0..i-1).
+struct BatchUnion {
+  std::vector<BatchDesc> hd;
+  BatchDesc *dd = nullptr;
+  pbng_bigraph ug{};
+};
+
+void batch_union(Arena &a, const pbng_bigraph *gs, uint32_t n, int mem, BatchUnion &B) {
+  B.hd.resize(n);
+  uint64_t nu = 0, nv = 0, m = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    const pbng_bigraph &g = gs[i];
+    if (!g.u_off || (g.m && !g.u_adj)) fail(PBNG_EINVAL, "graph %u: null pointer", i);
+    if ((uint64_t)g.nu + g.nv >= (1ull << 31) || g.m >= (1ull << 31)) fail(PBNG_EINVAL, "graph %u exceeds the size limits", i);
+    B.hd[i].nu = g.nu;
+    B.hd[i].nv = g.nv;
+    B.hd[i].m = (uint32_t)g.m;
+    B.hd[i].u_base = (uint32_t)nu;
+    B.hd[i].e_base = (uint32_t)m;
+    nu += g.nu;
+    m += g.m;
+    if (nu >= (1ull << 31) || m >= (1ull << 31)) fail(PBNG_EINVAL, "batch exceeds the size limits");
+  }
+  for (uint32_t i = 0; i < n; i++) {
+    B.hd[i].v_base = (uint32_t)nv;
+    nv += gs[i].nv;
+  }
+  if (nu + nv >= (1ull << 31)) fail(PBNG_EINVAL, "batch exceeds the size limits");
+  for (uint32_t i = 0; i < n; i++) {  // inputs on the device (copy host graphs first)
+    if (mem == PBNG_MEM_HOST) {
+      uint64_t *off = a.alloc<uint64_t>((size_t)gs[i].nu + 1);
+      uint32_t *adj = a.alloc<uint32_t>(gs[i].m ? gs[i].m : 1);
+      CK(cudaMemcpyAsync(off, gs[i].u_off, ((size_t)gs[i].nu + 1) * 8, cudaMemcpyHostToDevice, a.st));
+      if (gs[i].m) CK(cudaMemcpyAsync(adj, gs[i].u_adj, gs[i].m * 4, cudaMemcpyHostToDevice, a.st));
+      B.hd[i].u_off = off;
+      B.hd[i].u_adj = adj;
+    } else {
+      B.hd[i].u_off = gs[i].u_off;
+      B.hd[i].u_adj = gs[i].u_adj;
+    }
+  }
+  B.dd = a.alloc<BatchDesc>(n);
+  CK(cudaMemcpyAsync(B.dd, B.hd.data(), n * sizeof(BatchDesc), cudaMemcpyHostToDevice, a.st));
+  unsigned *chk = a.alloc<unsigned>(2);
+  const unsigned init[2] = {0xffffffffu, 0u};
+  CK(cudaMemcpyAsync(chk, init, sizeof(init), cudaMemcpyHostToDevice, a.st));
+  k_batch_validate<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(B.dd, n, chk, chk + 1);
+  CK_LAUNCH();
+  unsigned hchk[2];
+  CK(cudaMemcpyAsync(hchk, chk, sizeof(hchk), cudaMemcpyDeviceToHost, a.st));
+  CK(cudaStreamSynchronize(a.st));
+  if (hchk[0] != 0xffffffffu)
+    fail(PBNG_EINVAL, "graph %u: malformed CSR (%s%s%s)", hchk[0], (hchk[1] & BERR_OFFSETS) ? "bad offsets " : "",
+         (hchk[1] & BERR_RANGE) ? "neighbour id out of range " : "",
+         (hchk[1] & BERR_ORDER) ? "row not strictly increasing" : "");
+  uint64_t *uoff = a.alloc<uint64_t>(nu + 1);
+  uint32_t *uadj = a.alloc<uint32_t>(m ? m : 1);
+  k_union<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(B.dd, n, uoff, uadj);
+  CK_LAUNCH();
+  CK(cudaMemcpyAsync(uoff + nu, &m, 8, cudaMemcpyHostToDevice, a.st));
+  CK(cudaStreamSynchronize(a.st));
+  B.ug.nu = (uint32_t)nu;
+  B.ug.nv = (uint32_t)nv;
+  B.ug.m = m;
+  B.ug.u_off = uoff;
+  B.ug.u_adj = uadj;
+  check_graph(&B.ug);
+}
+
+void copy_bounds_out(const pbng_opts &o, const std::vector<uint64_t> &used) {
+  if (o.bounds_out)
+    for (size_t i = 0; i < used.size() && i < o.n_bounds_out; i++) o.bounds_out[i] = used[i];
+}
 }  // namespace
 }  // namespace pbng
 
@@ -474,67 +637,27 @@ extern "C" int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng
     if (!gs || !outs) fail(PBNG_EINVAL, "null graph or output array");
     if (side != PBNG_SIDE_U && side != PBNG_SIDE_V) fail(PBNG_EINVAL, "side must be PBNG_SIDE_U or PBNG_SIDE_V");
     TipParams p = tip_params(P, o);
+    for (uint32_t i = 0; i < n; i++)
+      if (!outs[i]) fail(PBNG_EINVAL, "graph %u: null output", i);
     init_device_pool();
     Arena a((cudaStream_t)o.stream);
     ProfScope ps(stats, a.st);
     Timer tm(a.st);
-    std::vector<BatchDesc> hd(n);
-    uint64_t nu = 0, nv = 0, m = 0;
-    for (uint32_t i = 0; i < n; i++) {
-      const pbng_bigraph &g = gs[i];
-      if (!g.u_off || (g.m && !g.u_adj) || !outs[i]) fail(PBNG_EINVAL, "graph %u: null pointer", i);
-      hd[i].nu = g.nu;
-      hd[i].nv = g.nv;
-      hd[i].m = (uint32_t)g.m;
-      hd[i].u_base = (uint32_t)nu;
-      hd[i].e_base = (uint32_t)m;
-      nu += g.nu;
-      m += g.m;
-      if (nu >= (1ull << 31) || m >= (1ull << 31)) fail(PBNG_EINVAL, "batch exceeds the size limits");
-    }
-    for (uint32_t i = 0; i < n; i++) {
-      hd[i].v_base = (uint32_t)nv;
-      nv += gs[i].nv;
-    }
-    if (nu + nv >= (1ull << 31)) fail(PBNG_EINVAL, "batch exceeds the size limits");
-    // inputs on the device (copy host graphs first)
-    for (uint32_t i = 0; i < n; i++) {
-      if (o.mem == PBNG_MEM_HOST) {
-        uint64_t *off = a.alloc<uint64_t>((size_t)gs[i].nu + 1);
-        uint32_t *adj = a.alloc<uint32_t>(gs[i].m ? gs[i].m : 1);
-        CK(cudaMemcpyAsync(off, gs[i].u_off, ((size_t)gs[i].nu + 1) * 8, cudaMemcpyHostToDevice, a.st));
-        if (gs[i].m) CK(cudaMemcpyAsync(adj, gs[i].u_adj, gs[i].m * 4, cudaMemcpyHostToDevice, a.st));
-        hd[i].u_off = off;
-        hd[i].u_adj = adj;
-      } else {
-        hd[i].u_off = gs[i].u_off;
-        hd[i].u_adj = gs[i].u_adj;
-      }
-    }
-    BatchDesc *dd = a.alloc<BatchDesc>(n);
-    CK(cudaMemcpyAsync(dd, hd.data(), n * sizeof(BatchDesc), cudaMemcpyHostToDevice, a.st));
-    uint64_t *uoff = a.alloc<uint64_t>(nu + 1);
-    uint32_t *uadj = a.alloc<uint32_t>(m ? m : 1);
-    k_union<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(dd, n, uoff, uadj);
-    CK_LAUNCH();
-    CK(cudaMemcpyAsync(uoff + nu, &m, 8, cudaMemcpyHostToDevice, a.st));
-    CK(cudaStreamSynchronize(a.st));
-    pbng_bigraph ug;
-    ug.nu = (uint32_t)nu;
-    ug.nv = (uint32_t)nv;
-    ug.m = m;
-    ug.u_off = uoff;
-    ug.u_adj = uadj;
+    BatchUnion B;
+    batch_union(a, gs, n, o.mem, B);
     Graph G;
-    build_graph(a, ug, true, false, G);
+    build_graph(a, B.ug, true, false, G);
+    CK(cudaStreamSynchronize(a.st));
+    uint64_t t_setup = tm.ns();
     uint32_t nx = side == PBNG_SIDE_U ? G.nu : G.nv;
     uint64_t *theta = a.alloc<uint64_t>(nx ? nx : 1);
     pbng_stats st;
     memset(&st, 0, sizeof(st));
+    std::vector<uint64_t> used;
+    p.bounds_used = &used;
     tip_decompose(a, G, side == PBNG_SIDE_U ? 0 : 1, p, theta, stats ? &st : nullptr);
     // per-graph outputs
     std::vector<uint64_t *> douts(n);
-    std::vector<uint64_t *> hbufs;
     for (uint32_t i = 0; i < n; i++) {
       if (o.mem == PBNG_MEM_HOST) {
         uint32_t cnt = side == PBNG_SIDE_U ? gs[i].nu : gs[i].nv;
@@ -545,7 +668,7 @@ extern "C" int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng
     }
     uint64_t **dptr = a.alloc<uint64_t *>(n);
     CK(cudaMemcpyAsync(dptr, douts.data(), n * sizeof(uint64_t *), cudaMemcpyHostToDevice, a.st));
-    k_scatter_out<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(theta, dd, n, dptr, side == PBNG_SIDE_U ? 0 : 1);
+    k_scatter_out<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(theta, B.dd, n, dptr, side == PBNG_SIDE_U ? 0 : 1);
     CK_LAUNCH();
     if (o.mem == PBNG_MEM_HOST)
       for (uint32_t i = 0; i < n; i++) {
@@ -553,8 +676,10 @@ extern "C" int pbng_tip_decompose_batch(const pbng_bigraph *gs, uint32_t n, pbng
         if (cnt) CK(cudaMemcpyAsync(outs[i], douts[i], (size_t)cnt * 8, cudaMemcpyDeviceToHost, a.st));
       }
     CK(cudaStreamSynchronize(a.st));
+    copy_bounds_out(o, used);
     if (stats) {
       *stats = st;
+      stats->ns_setup = t_setup;
       stats->ns_total = tm.ns();
       ps.fill();
     }
@@ -568,62 +693,24 @@ extern "C" int pbng_wing_decompose_batch(const pbng_bigraph *gs, uint32_t n, uin
     if (n == 0) return;
     if (!gs || !outs) fail(PBNG_EINVAL, "null graph or output array");
     TipParams p = tip_params(P, o);
+    for (uint32_t i = 0; i < n; i++)
+      if (gs[i].m && !outs[i]) fail(PBNG_EINVAL, "graph %u: null output", i);
     init_device_pool();
     Arena a((cudaStream_t)o.stream);
     ProfScope ps(stats, a.st);
     Timer tm(a.st);
-    std::vector<BatchDesc> hd(n);
-    uint64_t nu = 0, nv = 0, m = 0;
-    for (uint32_t i = 0; i < n; i++) {
-      const pbng_bigraph &g = gs[i];
-      if (!g.u_off || (g.m && (!g.u_adj || !outs[i]))) fail(PBNG_EINVAL, "graph %u: null pointer", i);
-      hd[i].nu = g.nu;
-      hd[i].nv = g.nv;
-      hd[i].m = (uint32_t)g.m;
-      hd[i].u_base = (uint32_t)nu;
-      hd[i].e_base = (uint32_t)m;
-      nu += g.nu;
-      m += g.m;
-      if (nu >= (1ull << 31) || m >= (1ull << 31)) fail(PBNG_EINVAL, "batch exceeds the size limits");
-    }
-    for (uint32_t i = 0; i < n; i++) {
-      hd[i].v_base = (uint32_t)nv;
-      nv += gs[i].nv;
-    }
-    if (nu + nv >= (1ull << 31)) fail(PBNG_EINVAL, "batch exceeds the size limits");
-    for (uint32_t i = 0; i < n; i++) {
-      if (o.mem == PBNG_MEM_HOST) {
-        uint64_t *off = a.alloc<uint64_t>((size_t)gs[i].nu + 1);
-        uint32_t *adj = a.alloc<uint32_t>(gs[i].m ? gs[i].m : 1);
-        CK(cudaMemcpyAsync(off, gs[i].u_off, ((size_t)gs[i].nu + 1) * 8, cudaMemcpyHostToDevice, a.st));
-        if (gs[i].m) CK(cudaMemcpyAsync(adj, gs[i].u_adj, gs[i].m * 4, cudaMemcpyHostToDevice, a.st));
-        hd[i].u_off = off;
-        hd[i].u_adj = adj;
-      } else {
-        hd[i].u_off = gs[i].u_off;
-        hd[i].u_adj = gs[i].u_adj;
-      }
-    }
-    BatchDesc *dd = a.alloc<BatchDesc>(n);
-    CK(cudaMemcpyAsync(dd, hd.data(), n * sizeof(BatchDesc), cudaMemcpyHostToDevice, a.st));
-    uint64_t *uoff = a.alloc<uint64_t>(nu + 1);
-    uint32_t *uadj = a.alloc<uint32_t>(m ? m : 1);
-    k_union<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(dd, n, uoff, uadj);
-    CK_LAUNCH();
-    CK(cudaMemcpyAsync(uoff + nu, &m, 8, cudaMemcpyHostToDevice, a.st));
-    CK(cudaStreamSynchronize(a.st));
-    pbng_bigraph ug;
-    ug.nu = (uint32_t)nu;
-    ug.nv = (uint32_t)nv;
-    ug.m = m;
-    ug.u_off = uoff;
-    ug.u_adj = uadj;
-    check_graph(&ug);
+    BatchUnion B;
+    batch_union(a, gs, n, o.mem, B);
+    const uint64_t m = B.ug.m;
     Graph G;
-    build_graph(a, ug, true, true, G);
+    build_graph(a, B.ug, true, true, G);
+    CK(cudaStreamSynchronize(a.st));
+    uint64_t t_setup = tm.ns();
     uint64_t *wing = a.alloc<uint64_t>(m ? m : 1);
     pbng_stats st;
     memset(&st, 0, sizeof(st));
+    std::vector<uint64_t> used;
+    p.bounds_used = &used;
     if (m) pbng::wing_decompose(a, G, p, wing, stats ? &st : nullptr);
     std::vector<uint64_t *> douts(n);
     for (uint32_t i = 0; i < n; i++)
@@ -631,15 +718,17 @@ extern "C" int pbng_wing_decompose_batch(const pbng_bigraph *gs, uint32_t n, uin
     uint64_t **dptr = a.alloc<uint64_t *>(n);
     CK(cudaMemcpyAsync(dptr, douts.data(), n * sizeof(uint64_t *), cudaMemcpyHostToDevice, a.st));
     if (m) {
-      k_scatter_edges<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(wing, dd, n, dptr);
+      k_scatter_edges<<<std::min<uint32_t>(n, 8 * num_sms()), 256, 0, a.st>>>(wing, B.dd, n, dptr);
       CK_LAUNCH();
     }
     if (o.mem == PBNG_MEM_HOST)
       for (uint32_t i = 0; i < n; i++)
         if (gs[i].m) CK(cudaMemcpyAsync(outs[i], douts[i], (size_t)gs[i].m * 8, cudaMemcpyDeviceToHost, a.st));
     CK(cudaStreamSynchronize(a.st));
+    copy_bounds_out(o, used);
     if (stats) {
       *stats = st;
+      stats->ns_setup = t_setup;
       stats->ns_total = tm.ns();
       ps.fill();
     }

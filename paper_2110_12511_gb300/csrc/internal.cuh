@@ -162,10 +162,12 @@ struct TipParams {
   int recount, compact, graph_rounds;
   uint32_t bucket_shift;  // 0 = automatic
   uint32_t warp_max_w, group_max_w, item_w;  // coarse-peel schedule, 0 = default
+  uint32_t fd_cluster_min;                   // fine phase: smallest partition for a cluster team
   uint64_t timeout_ns;
   const float *mlp_params;  // learned bounds (bounds_mode == PBNG_BOUNDS_LEARNED)
   uint32_t mlp_hidden, mlp_out;
   std::vector<uint64_t> *bounds_used;  // optional record of theta(2..) used
+  bool coarse_only = false;            // stop after the coarse phase (no tip numbers written)
 };
 void tip_decompose(Arena &a, Graph &G, int side, const TipParams &p, uint64_t *theta_out, pbng_stats *st);
 
@@ -185,6 +187,18 @@ std::vector<uint64_t> propose_bounds(Arena &a, const float *params, uint32_t hid
                                      uint64_t max_support);
 
 // ------------------------------------------------------------------ wing
+// BE-Index (Sec. 2.3): blooms with their numbers k0 and first twin pair boff,
+// twin pairs (pe1[q], pe2[q]) of bloom pbloom[q], and every edge's pairs
+// elink[eoff[e] .. eoff[e+1]).
+struct BEIndex {
+  uint32_t nb = 0;
+  size_t np = 0;
+  uint32_t *k0 = nullptr, *boff = nullptr, *pe1 = nullptr, *pe2 = nullptr, *pbloom = nullptr;
+  uint32_t *eoff = nullptr, *elink = nullptr;
+};
+void be_index_build(Arena &a, const Graph &G, unsigned long long *sup_e, uint64_t *cctr, BEIndex &I);
+// out_e[e] = sum over the blooms B of e of (k_B - 1); *total = sum over blooms of C(k_B, 2)
+void be_index_sums(Arena &a, const Graph &G, uint64_t *out_e, uint64_t *total, pbng_stats *st);
 void wing_decompose(Arena &a, Graph &G, const TipParams &p, uint64_t *theta_out, pbng_stats *st);
 
 }  // namespace pbng

@@ -959,6 +959,8 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
   __syncthreads();
   WarpGrp wg;
   BlockGrp<FT> bg{ws, ws64};
+  __shared__ TeamMin tmin;
+  BlockTeam T{&S, S.hist, &tmin};
   ull my_wedges = 0, my_updates = 0, my_steps = 0;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -987,7 +989,9 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
     while (S.na + S.nc > 0) {
       p_steps++;
       // every vertex at the running minimum is peeled with tip number = level
-      uint32_t nf = fd_select<FT>(S, L, A.sup, A.theta, A.state, ST_PEELED, ST_PEELED);
+      uint32_t nf = fd_select(T, L, A.sup, A.theta, A.state, ST_PEELED, ST_PEELED, WIN_CAP);
+      uint32_t *cand = L.c[S.pc];
+      const ull hi = S.hi;
       if (threadIdx.x == 0) {
         s_fidx = 0;
         s_nbig = 0;
@@ -1024,7 +1028,7 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
             uint32_t c = wval[i];
             if (c >= 2) {
               ull dec = choose2(c);
-              fd_crossing(S, L, kk, atomicAdd(&A.sup[kk], (ull)(0ull - dec)), dec);
+              fd_crossing(&S.nc, cand, hi, kk, atomicAdd(&A.sup[kk], (ull)(0ull - dec)), dec);
               my_updates++;
             }
             wkey[i] = EMPTY_KEY;
@@ -1054,7 +1058,7 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
             uint32_t c = atomicExch(&cnt[A.loc[xp]], 0u);
             if (c >= 2) {
               ull dec = choose2(c);
-              fd_crossing(S, L, xp, atomicAdd(&A.sup[xp], (ull)(0ull - dec)), dec);
+              fd_crossing(&S.nc, cand, hi, xp, atomicAdd(&A.sup[xp], (ull)(0ull - dec)), dec);
               my_updates++;
             }
           });
@@ -1146,7 +1150,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   uint32_t nx = side == 0 ? G.nu : G.nv, ny = side == 0 ? G.nv : G.nu;
   if (nx == 0) return;
   if (G.m == 0) {
-    CK(cudaMemsetAsync(theta_out, 0, (size_t)nx * 8, a.st));
+    if (theta_out) CK(cudaMemsetAsync(theta_out, 0, (size_t)nx * 8, a.st));
     return;
   }
   const uint32_t *p_off = side == 0 ? G.u_off : G.v_off, *p_adj = side == 0 ? G.u_adj : G.v_adj;
@@ -1586,6 +1590,11 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   }
   uint32_t nparts = pi;
   CK(cudaEventRecord(ev[2], a.st));
+  if (prm.coarse_only) {  // the bounds were all that was asked for
+    CK(cudaStreamSynchronize(a.st));
+    for (auto &e : ev) cudaEventDestroy(e);
+    return;
+  }
 
   // ---- fine phase: partitions, induced subgraphs, LPT queue
   uint32_t *pcnt = a.zeros<uint32_t>(nparts + 1), *ps = a.alloc<uint32_t>(nparts + 1);
@@ -1669,6 +1678,15 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   g_prof.end();
   CK(cudaEventRecord(ev[4], a.st));
   CK(cudaStreamSynchronize(a.st));
+  if (trace) {  // fine-phase line per partition: side partition |X_p| work steps cycles
+    std::vector<ull> pst(2 * (size_t)nparts);
+    std::vector<uint32_t> hps(nparts + 1);
+    CK(cudaMemcpy(pst.data(), pstat, pst.size() * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hps.data(), ps, hps.size() * 4, cudaMemcpyDeviceToHost));
+    for (uint32_t i = 0; i < nparts; i++)
+      fprintf(trace, "F %d %u %u %llu %llu %llu\n", side, i, hps[i + 1] - hps[i], (unsigned long long)hwork[i],
+              (unsigned long long)pst[2 * i], (unsigned long long)pst[2 * i + 1]);
+  }
   if (st) {
     ull hd[10];
     CK(cudaMemcpy(hd, dwedge, sizeof(hd), cudaMemcpyDeviceToHost));

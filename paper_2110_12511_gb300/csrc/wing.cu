@@ -28,6 +28,8 @@
 //  every step peels all edges at the minimum support together, applying the
 //  same two-pass update restricted to I_i.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "fdwin.cuh"
@@ -517,150 +519,148 @@ struct WFDArgs {
   ull *pstat;  // per partition: steps, SM cycles
   const uint32_t *foff, *flink;  // per edge: its links in its own partition's index
   uint32_t *glen;                // live prefix of each group's pair list in order
-  uint32_t *gdead;               // pairs removed since the group's last compaction
   uint32_t *order_w;             // writable alias of order (compaction)
 };
 
 constexpr int WFT = 512;
+constexpr int WFD_PSTAT = 7;  // per-partition statistics of the fine phase
 
-__global__ void __launch_bounds__(WFT) k_wing_fd(WFDArgs A) {
-  __shared__ uint32_t s_p, s_nt, s_nc;
-  __shared__ FDShared S;
-  __shared__ uint32_t s_itm[WFT], s_lo[WFT], s_pre[WFT + 1];
-  __shared__ uint32_t ws[WFT / 32 + 2];
-  __shared__ ull ws64[WFT / 32];
-  BlockGrp<WFT> bg{ws, ws64};
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Fine phase of the partitions handed out by A.queue / A.orderp (Alg. 5 lines
+// 1-11 with the batch rule of Sec. 5.1), one partition at a time per team.
+// Every step: the selection (fd_select), pass 1 over the links of the peeled
+// edges inside I_p, pass 2 over the touched groups' live pairs, the groups'
+// bloom numbers and lazy compaction, then the peeled state.  A cluster team
+// splits every phase across its blocks (each block computes the same scan of
+// a chunk and takes an interleaved share of its flattened work).
+template <class Team>
+__device__ void wing_fd_run(const WFDArgs &A, const Team &T, uint32_t cap, uint32_t *s_itm, uint32_t *s_lo,
+                            uint32_t *s_pre, const BlockGrp<WFT> &bg) {
+  FDShared *S = T.S;
+  const int lane = threadIdx.x & 31;
+  const uint32_t nthr = T.nthr();
   ull links = 0, ups = 0, steps = 0;
   for (;;) {
-    if (threadIdx.x == 0) {
+    if (T.leader()) {
       unsigned q = atomicAdd(A.queue, 1u);
-      s_p = q < A.nparts ? A.orderp[q] : 0xffffffffu;
+      S->p = q < A.nparts ? A.orderp[q] : 0xffffffffu;
     }
-    __syncthreads();
-    uint32_t p = s_p;
+    T.sync();
+    const uint32_t p = *(volatile uint32_t *)&S->p;
+    T.sync();  // every block has read p before it can change, or before the team exits
     if (p == 0xffffffffu) break;
-    uint32_t base = A.ps[p], np = A.ps[p + 1] - base;
+    const uint32_t base = A.ps[p], np = A.ps[p + 1] - base;
     uint32_t *lf = A.buf_f + base, *gt = A.gtouch + 2 * A.gps[p];
     FDLists L{{A.buf_a + base, A.buf_b + base}, {A.buf_c + base, A.buf_d + base}, lf};
-    for (uint32_t j = threadIdx.x; j < np; j += WFT) L.a[0][j] = A.es[base + j];
-    if (threadIdx.x == 0) {
-      S.na = np;
-      S.nc = 0;
-      S.pa = 0;
-      S.pc = 0;
-      S.level = 0;
+    for (uint32_t j = T.tid(); j < np; j += nthr) L.a[0][j] = A.es[base + j];
+    if (T.leader()) {
+      S->na = np;
+      S->nc = 0;
+      S->pa = 0;
+      S->pc = 0;
+      S->level = 0;
     }
     long long t_part = clock64();
-    ull p_steps = 0;
-    __syncthreads();
-    while (S.na + S.nc > 0) {
+    ull p_steps = 0, cyc[4] = {0, 0, 0, 0}, rescans = 0;
+    T.sync();
+    for (;;) {
+      if (*(volatile uint32_t *)&S->na + *(volatile uint32_t *)&S->nc == 0) break;
       p_steps++;
-      uint32_t nf = fd_select<WFT>(S, L, A.sup, A.theta, A.state, ST_ACTIVE, ST_PEELED);
-      if (threadIdx.x == 0) s_nt = 0;
-      __syncthreads();
+      long long t0 = clock64();
+      rescans += *(volatile uint32_t *)&S->nc == 0;
+      const uint32_t nf = fd_select(T, L, A.sup, A.theta, A.state, ST_ACTIVE, ST_PEELED, cap);
+      long long t1 = clock64();
+      uint32_t *cand = L.c[*(volatile uint32_t *)&S->pc];
+      const ull hi = *(volatile ull *)&S->hi;
       steps++;
       // pass 1 restricted to I_p, flattened over (peeled edge, link) so the
-      // whole block shares a few long link lists
+      // whole team shares a few long link lists
       for (uint32_t c0 = 0; c0 < nf; c0 += WFT) {
         uint32_t r = threadIdx.x, lo = 0, len = 0;
         if (c0 + r < nf) {
-          uint32_t e = lf[c0 + r];
+          uint32_t e = ldt(&lf[c0 + r]);
           s_itm[r] = e;
           lo = A.foff[e];
           len = A.foff[e + 1] - lo;
         }
         s_lo[r] = lo;
-        uint32_t T = bg.scan(len, s_pre);
-        for (uint32_t w = r; w < T; w += WFT) {
+        const uint32_t Tw = bg.scan(len, s_pre);
+        for (uint32_t w = T.tid(); w < Tw; w += nthr) {
           int i = seg_of(s_pre, WFT, w);
           uint32_t e = s_itm[i], q = A.flink[s_lo[i] + (w - s_pre[i])];  // a link of e in I_p
           links++;
-          if (!*(volatile uint8_t *)&A.palive[q]) continue;
+          if (!ldt(&A.palive[q])) continue;
           uint32_t a = A.pe1[q], b = A.pe2[q];
           uint32_t et = a == e ? b : a;
           bool in_p = A.part[et] == p;
-          uint8_t st = in_p ? *(volatile uint8_t *)&A.state[et] : (uint8_t)ST_ALIVE;
+          uint8_t st = in_p ? ldt(&A.state[et]) : (uint8_t)ST_ALIVE;
           if (st == ST_ACTIVE && et > e) continue;
           uint32_t g = A.pb_of[q];
           A.palive[q] = 0;
           if (in_p && st == ST_ALIVE) {
-            uint32_t kb = A.gk[g];
+            uint32_t kb = ldt(&A.gk[g]);
             if (kb >= 2) {
               ull old = atomicAdd(&A.sup[et], (ull)(0ull - (ull)(kb - 1)));
-              fd_crossing(S, L, et, old, kb - 1);
+              fd_crossing(&S->nc, cand, hi, et, old, kb - 1);
               ups++;
             }
           }
-          if (atomicAdd(&A.gcnt[g], 1u) == 0u) gt[atomicAdd(&s_nt, 1u)] = g;
+          if (atomicAdd(&A.gcnt[g], 1u) == 0u) gt[atomicAdd(&S->nt, 1u)] = g;
         }
-        __syncthreads();
+        __syncthreads();  // the chunk arrays are rewritten by the next chunk
       }
-      // pass 2 restricted to I_p, flattened over (touched group, live pair)
-      uint32_t nt = s_nt;
-      for (uint32_t c0 = 0; c0 < nt; c0 += WFT) {
-        uint32_t r = threadIdx.x, lo = 0, len = 0;
-        if (c0 + r < nt) {
-          uint32_t g = gt[c0 + r];
-          s_itm[r] = g;
-          lo = A.gstart[g];
-          len = A.glen[g];
-        }
-        s_lo[r] = lo;
-        uint32_t T = bg.scan(len, s_pre);
-        for (uint32_t w = r; w < T; w += WFT) {
-          int i = seg_of(s_pre, WFT, w);
-          uint32_t g = s_itm[i], q = A.order_w[s_lo[i] + (w - s_pre[i])];
-          links++;
-          if (!A.palive[q]) continue;
-          uint32_t c = A.gcnt[g];
-          uint32_t a = A.pe1[q], b = A.pe2[q];
-          if (A.part[a] == p && A.state[a] == ST_ALIVE) fd_crossing(S, L, a, atomicAdd(&A.sup[a], (ull)(0ull - c)), c), ups++;
-          if (A.part[b] == p && A.state[b] == ST_ALIVE) fd_crossing(S, L, b, atomicAdd(&A.sup[b], (ull)(0ull - c)), c), ups++;
-        }
-        __syncthreads();
-      }
-      // bloom numbers, and lazy compaction of groups a quarter dead
-      if (threadIdx.x == 0) s_nc = 0;
-      __syncthreads();
-      for (uint32_t j = threadIdx.x; j < nt; j += WFT) {
-        uint32_t g = gt[j], c = A.gcnt[g];
-        A.gk[g] -= c;
-        A.gcnt[g] = 0;
-        uint32_t d = A.gdead[g] + c;
-        A.gdead[g] = d;
-        if (4 * d >= A.glen[g]) gt[nt + atomicAdd(&s_nc, 1u)] = g;  // queued after the touched list
-      }
-      __syncthreads();
-      uint32_t nc = s_nc;
-      for (uint32_t j = warp; j < nc; j += WFT / 32) {
-        uint32_t g = gt[nt + j];
-        uint32_t lo = A.gstart[g], len = A.glen[g], out = 0;
+      T.sync();
+      long long t2 = clock64();
+      // pass 2 restricted to I_p (Alg. 6, second loop) with the bloom numbers:
+      // a warp per touched group walks its pair list in 32-pair chunks
+      // (coalesced), lowers both edges of every live pair by count[g], and
+      // compacts the list in the same walk
+      const uint32_t nt = *(volatile uint32_t *)&S->nt;
+      for (uint32_t j = T.tid() >> 5; j < nt; j += nthr >> 5) {
+        const uint32_t g = ldt(&gt[j]);
+        const uint32_t c = ldt(&A.gcnt[g]), lo = A.gstart[g], len = ldt(&A.glen[g]);
+        uint32_t out = 0;
         for (uint32_t k = 0; k < len; k += 32) {
           uint32_t q = 0;
           bool live = false;
           if (k + lane < len) {
-            q = A.order_w[lo + k + lane];
-            live = A.palive[q];
+            q = ldt(&A.order_w[lo + k + lane]);
+            live = ldt(&A.palive[q]);
+            links++;
           }
-          unsigned bal = __ballot_sync(0xffffffffu, live);
-          __syncwarp();
+          if (live) {
+            const uint32_t ea = A.pe1[q], eb = A.pe2[q];
+            if (A.part[ea] == p && ldt(&A.state[ea]) == ST_ALIVE)
+              fd_crossing(&S->nc, cand, hi, ea, atomicAdd(&A.sup[ea], (ull)(0ull - c)), c), ups++;
+            if (A.part[eb] == p && ldt(&A.state[eb]) == ST_ALIVE)
+              fd_crossing(&S->nc, cand, hi, eb, atomicAdd(&A.sup[eb], (ull)(0ull - c)), c), ups++;
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, live);
           if (live) A.order_w[lo + out + __popc(bal & ((1u << lane) - 1u))] = q;
           out += __popc(bal);
           __syncwarp();
         }
         if (lane == 0) {
           A.glen[g] = out;
-          A.gdead[g] = 0;
+          A.gk[g] = ldt(&A.gk[g]) - c;
+          A.gcnt[g] = 0;
         }
       }
-      __syncthreads();
-      for (uint32_t j = threadIdx.x; j < nf; j += WFT) A.state[lf[j]] = ST_PEELED;
-      __syncthreads();
+      T.sync();
+      long long t3 = clock64();
+      for (uint32_t j = T.tid(); j < nf; j += nthr) A.state[ldt(&lf[j])] = ST_PEELED;
+      T.sync();
+      long long t4 = clock64();
+      cyc[0] += t1 - t0;
+      cyc[1] += t2 - t1;
+      cyc[2] += t3 - t2;
+      cyc[3] += t4 - t3;
     }
-    if (threadIdx.x == 0 && A.pstat) {
-      A.pstat[2 * p] = p_steps;
-      A.pstat[2 * p + 1] = (ull)(clock64() - t_part);
+    if (T.leader() && A.pstat) {  // steps, cycles; then select, pass 1, pass 2, rest, window rescans
+      ull *ps = A.pstat + (size_t)WFD_PSTAT * p;
+      ps[0] = p_steps;
+      ps[1] = (ull)(clock64() - t_part);
+      for (int k = 0; k < 4; k++) ps[2 + k] = cyc[k];
+      ps[6] = rescans;
     }
   }
   for (int o = 16; o; o >>= 1) links += __shfl_xor_sync(0xffffffffu, links, o), ups += __shfl_xor_sync(0xffffffffu, ups, o);
@@ -668,27 +668,89 @@ __global__ void __launch_bounds__(WFT) k_wing_fd(WFDArgs A) {
     if (links) atomicAdd(&A.ctr[0], links);
     if (ups) atomicAdd(&A.ctr[1], ups);
   }
-  if (threadIdx.x == 0) atomicAdd(&A.ctr[2], steps);
+  if (T.leader()) atomicAdd(&A.ctr[2], steps);
+}
+
+// one block per partition
+__global__ void __launch_bounds__(WFT) k_wing_fd(WFDArgs A, uint32_t cap) {
+  __shared__ FDShared S;
+  __shared__ uint32_t s_itm[WFT], s_lo[WFT], s_pre[WFT + 1];
+  __shared__ uint32_t ws[WFT / 32 + 2];
+  __shared__ ull ws64[WFT / 32];
+  __shared__ TeamMin tmin;
+  BlockGrp<WFT> bg{ws, ws64};
+  BlockTeam T{&S, S.hist, &tmin};
+  wing_fd_run(A, T, cap, s_itm, s_lo, s_pre, bg);
+}
+
+// one thread-block cluster per (heavy) partition; the step state lives in
+// the shared memory of the cluster's first block
+__global__ void __launch_bounds__(WFT) k_wing_fd_cluster(WFDArgs A, uint32_t cap) {
+  __shared__ FDShared S;
+  __shared__ uint32_t lhist[65];
+  __shared__ uint32_t s_itm[WFT], s_lo[WFT], s_pre[WFT + 1];
+  __shared__ uint32_t ws[WFT / 32 + 2];
+  __shared__ ull ws64[WFT / 32];
+  BlockGrp<WFT> bg{ws, ws64};
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  __shared__ TeamMin tmin;
+  ClusterTeam T{cl.map_shared_rank(&S, 0), lhist, &tmin, cl.block_rank(), cl.num_blocks()};
+  wing_fd_run(A, T, cap, s_itm, s_lo, s_pre, bg);
+}
+
+// candidate window of a cluster team, in units of WIN_CAP per block
+#ifndef FD_CLUSTER_CAP_MULT
+#define FD_CLUSTER_CAP_MULT 2
+#endif
+
+// Cluster size for heavy partitions (16 blocks where the device can hold
+// such clusters, else 8, else 1 = no clusters) and how many clusters run at
+// once (at most half of the SMs, so that light partitions keep the rest).
+struct FDCluster {
+  uint32_t size = 1, max_clusters = 0;
+};
+FDCluster fd_cluster_shape() {
+  static FDCluster fc;
+  static bool done = false;
+  if (done) return fc;
+  done = true;
+  if (cudaFuncSetAttribute(k_wing_fd_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    cudaGetLastError();
+  for (uint32_t cs : {16u, 8u}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(WFT);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_wing_fd_cluster, &cfg) == cudaSuccess && n > 0) {
+      fc.size = cs;
+      fc.max_clusters = std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)n, (uint32_t)num_sms() / (2 * cs)));
+      return fc;
+    }
+    cudaGetLastError();
+  }
+  return fc;
 }
 
 }  // namespace
 
-// --------------------------------------------------------------- driver
-void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_out, pbng_stats *st) {
+// BE-Index of G (Sec. 2.3, "Construction of BE-Index"): per-edge butterfly
+// counts into sup (zeroed by the caller; Alg. 1) and counters into cctr[0..2],
+// then the blooms (k0, first pair boff), their twin pairs (pe1, pe2, pbloom)
+// and the edge -> pair lists (eoff, elink).
+void be_index_build(Arena &a, const Graph &G, unsigned long long *sup, uint64_t *cctr, BEIndex &I) {
   const int T = 256;
   const int sms = num_sms();
   const unsigned cap = 16 * sms;
-  uint32_t m = G.m, n = G.n;
-  if (m == 0) return;
-  cudaEvent_t ev[5];
-  for (auto &e : ev) CK(cudaEventCreate(&e));
-  CK(cudaEventRecord(ev[0], a.st));
-
-  // ---- per-edge counts and BE-Index sizes (Alg. 1 + Sec. 2.3 construction)
-  ull *sup = a.zeros<ull>(m), *init = a.alloc<ull>(m);
+  const uint32_t m = G.m, n = G.n;
   uint64_t *cnt_lab = a.zeros<uint64_t>(n);
   ull *be_nb = a.zeros<ull>((size_t)n + 1), *be_np = a.zeros<ull>((size_t)n + 1);
-  uint64_t *cctr = a.zeros<uint64_t>(4);
   CountOut co;
   co.cnt_lab = cnt_lab;
   co.cnt_e = (uint64_t *)sup;
@@ -708,8 +770,8 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   if (nblooms >= (1ull << 32) || 2 * npairs >= (1ull << 32))
     fail(PBNG_EOVERFLOW, "BE-Index with %llu blooms and %llu twin pairs exceeds the 32-bit index limit",
          (unsigned long long)nblooms, (unsigned long long)npairs);
-  uint32_t nb = (uint32_t)nblooms;
-  size_t np = (size_t)npairs;
+  const uint32_t nb = (uint32_t)nblooms;
+  const size_t np = (size_t)npairs;
   uint32_t *k0 = a.alloc<uint32_t>((size_t)nb + 1), *boff = a.alloc<uint32_t>((size_t)nb + 1);
   uint32_t *pe1 = a.alloc<uint32_t>(np + 1), *pe2 = a.alloc<uint32_t>(np + 1), *pbloom = a.alloc<uint32_t>(np + 1);
   if (np) {
@@ -776,6 +838,88 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   a.free(pb);
   a.free(be_nb);
   a.free(be_np);
+  I.nb = nb;
+  I.np = np;
+  I.k0 = k0;
+  I.boff = boff;
+  I.pe1 = pe1;
+  I.pe2 = pe2;
+  I.pbloom = pbloom;
+  I.eoff = eoff;
+  I.elink = elink;
+}
+
+namespace {
+// Prop. 1-2 sums of the BE-Index: per edge, sum over its blooms of (k_B - 1);
+// over all blooms, sum of C(k_B, 2)
+__global__ void k_be_edge_sums(const uint32_t *pe1, const uint32_t *pe2, const uint32_t *pbloom, const uint32_t *k0,
+                               size_t np, ull *out_e) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < np; q += (size_t)gridDim.x * blockDim.x) {
+    ull k = k0[pbloom[q]] - 1ull;
+    atomicAdd(&out_e[pe1[q]], k);
+    atomicAdd(&out_e[pe2[q]], k);
+  }
+}
+
+__global__ void k_be_bloom_sum(const uint32_t *k0, uint32_t nb, ull *out) {
+  ull s = 0;
+  for (size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x; b < nb; b += (size_t)gridDim.x * blockDim.x) {
+    ull k = k0[b];
+    s += k * (k - 1) / 2;
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+}  // namespace
+
+void be_index_sums(Arena &a, const Graph &G, uint64_t *out_e, uint64_t *total, pbng_stats *st) {
+  const int T = 256;
+  const unsigned cap = 16 * num_sms();
+  const uint32_t m = G.m;
+  *total = 0;
+  if (m == 0) return;
+  ull *sup = a.zeros<ull>(m);
+  uint64_t *cctr = a.zeros<uint64_t>(4);
+  BEIndex I;
+  be_index_build(a, G, sup, cctr, I);
+  CK(cudaMemsetAsync(out_e, 0, (size_t)m * 8, a.st));
+  ull *tot = a.zeros<ull>(1);
+  if (I.np) {
+    k_be_edge_sums<<<grid_for(I.np, T, cap), T, 0, a.st>>>(I.pe1, I.pe2, I.pbloom, I.k0, I.np, (ull *)out_e);
+    CK_LAUNCH();
+  }
+  if (I.nb) {
+    k_be_bloom_sum<<<grid_for(I.nb, T, cap), T, 0, a.st>>>(I.k0, I.nb, tot);
+    CK_LAUNCH();
+  }
+  CK(cudaMemcpyAsync(total, tot, 8, cudaMemcpyDeviceToHost, a.st));
+  CK(cudaStreamSynchronize(a.st));
+  if (st) {
+    st->links = 2 * (uint64_t)I.np;
+    st->blooms = I.nb;
+  }
+}
+
+// --------------------------------------------------------------- driver
+void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_out, pbng_stats *st) {
+  const int T = 256;
+  const int sms = num_sms();
+  const unsigned cap = 16 * sms;
+  uint32_t m = G.m, n = G.n;
+  if (m == 0) return;
+  cudaEvent_t ev[5];
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(ev[0], a.st));
+
+  // ---- per-edge counts and the BE-Index (Alg. 1 + Sec. 2.3 construction)
+  ull *sup = a.zeros<ull>(m), *init = a.alloc<ull>(m);
+  uint64_t *cctr = a.zeros<uint64_t>(4);
+  BEIndex I;
+  be_index_build(a, G, sup, cctr, I);
+  const uint32_t nb = I.nb;
+  const size_t np = I.np;
+  uint32_t *k0 = I.k0, *boff = I.boff, *pe1 = I.pe1, *pe2 = I.pe2, *pbloom = I.pbloom, *eoff = I.eoff,
+           *elink = I.elink;
   CK(cudaEventRecord(ev[1], a.st));
 
   // ---- coarse phase
@@ -954,11 +1098,21 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   std::vector<ull> hwork(nparts);
   CK(cudaMemcpyAsync(hwork.data(), work, (size_t)nparts * 8, cudaMemcpyDeviceToHost, a.st));
   CK(cudaStreamSynchronize(a.st));
+  // LPT order (heaviest first), split into partitions large enough for a
+  // cluster of blocks and the rest (one block each)
+  std::vector<uint32_t> hps(nparts + 1);
+  CK(cudaMemcpyAsync(hps.data(), ps, ((size_t)nparts + 1) * 4, cudaMemcpyDeviceToHost, a.st));
+  CK(cudaStreamSynchronize(a.st));
   std::vector<uint32_t> ord(nparts);
   for (uint32_t i = 0; i < nparts; i++) ord[i] = i;
   std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return hwork[x] > hwork[y]; });
+  const FDCluster fc = fd_cluster_shape();
+  std::vector<uint32_t> heavy, light;
+  for (uint32_t i : ord) (fc.size > 1 && hps[i + 1] - hps[i] >= prm.fd_cluster_min ? heavy : light).push_back(i);
+  std::vector<uint32_t> both(heavy);
+  both.insert(both.end(), light.begin(), light.end());
   uint32_t *dord = a.alloc<uint32_t>(nparts);
-  CK(cudaMemcpyAsync(dord, ord.data(), (size_t)nparts * 4, cudaMemcpyHostToDevice, a.st));
+  CK(cudaMemcpyAsync(dord, both.data(), (size_t)nparts * 4, cudaMemcpyHostToDevice, a.st));
   CK(cudaEventRecord(ev[3], a.st));
 
   // ---- fine phase (Alg. 5 lines 1-11)
@@ -994,9 +1148,9 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   W.gtouch = gtouch;
   W.nparts = nparts;
   W.queue = dc + 8;
-  CK(cudaMemsetAsync(dc + 8, 0, 4, a.st));
+  CK(cudaMemsetAsync(dc + 8, 0, 8, a.st));  // queues of the light and heavy partitions
   W.ctr = wctr + 4;
-  ull *pstat = a.zeros<ull>(2 * (size_t)nparts);
+  ull *pstat = a.zeros<ull>((size_t)WFD_PSTAT * nparts);
   W.pstat = pstat;
   {
     uint32_t *fdeg = a.zeros<uint32_t>((size_t)m + 1), *foff = a.alloc<uint32_t>((size_t)m + 1);
@@ -1016,15 +1170,72 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
       CK_LAUNCH();
     }
     W.glen = glen;
-    W.gdead = a.zeros<uint32_t>((size_t)ngroups + 1);
     W.order_w = order;
   }
   g_prof.begin(PROF_FD);
-  k_wing_fd<<<std::min<unsigned>(nparts, 2 * sms), WFT, 0, a.st>>>(W);
-  CK_LAUNCH();
+  {
+    // heavy partitions: clusters of fc.size blocks on a side stream; the rest:
+    // one block each on the call's stream, concurrently
+    const uint32_t nh = (uint32_t)heavy.size(), nl = (uint32_t)light.size();
+    const uint32_t ncl = std::min<uint32_t>(nh, fc.max_clusters);
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (ncl) {
+      CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+      CK(cudaEventRecord(fork, a.st));
+      CK(cudaStreamWaitEvent(side, fork, 0));
+      WFDArgs WH = W;
+      WH.orderp = dord;
+      WH.nparts = nh;
+      WH.queue = dc + 9;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(ncl * fc.size);
+      cfg.blockDim = dim3(WFT);
+      cfg.stream = side;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = fc.size;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      CK(cudaLaunchKernelEx(&cfg, k_wing_fd_cluster, WH, WIN_CAP * fc.size * FD_CLUSTER_CAP_MULT));
+      CK_LAUNCH();
+      CK(cudaEventRecord(join, side));
+    }
+    if (nl) {
+      WFDArgs WL = W;
+      WL.orderp = dord + nh;
+      WL.nparts = nl;
+      unsigned blocks = std::max<unsigned>(1u, std::min<unsigned>(nl, 2 * sms - ncl * fc.size));
+      k_wing_fd<<<blocks, WFT, 0, a.st>>>(WL, WIN_CAP);
+      CK_LAUNCH();
+    }
+    if (ncl) {
+      CK(cudaStreamWaitEvent(a.st, join, 0));
+      cudaEventDestroy(fork);
+      cudaEventDestroy(join);
+      cudaStreamDestroy(side);
+    }
+  }
   g_prof.end();
   CK(cudaEventRecord(ev[4], a.st));
   CK(cudaStreamSynchronize(a.st));
+  if (const char *tp = getenv("PBNG_TRACE")) {  // fine-phase line per partition: partition |E_p| work steps cycles
+    if (FILE *f = fopen(tp, "a")) {
+      std::vector<ull> pst((size_t)WFD_PSTAT * nparts);
+      CK(cudaMemcpy(pst.data(), pstat, pst.size() * 8, cudaMemcpyDeviceToHost));
+      // partition |E_p| work steps cycles | cycles of select, pass 1, pass 2, rest | rescans
+      for (uint32_t i = 0; i < nparts; i++) {
+        const ull *q = &pst[(size_t)WFD_PSTAT * i];
+        fprintf(f, "W %u %u %llu %llu %llu %llu %llu %llu %llu %llu\n", i, hps[i + 1] - hps[i],
+                (unsigned long long)hwork[i], q[0], q[1], q[2], q[3], q[4], q[5], q[6]);
+      }
+      fclose(f);
+    }
+  }
   if (st) {
     ull hw[8];
     uint64_t hcc[3];
@@ -1053,11 +1264,11 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
       st->fd_work_sum += hwork[i];
       if (hwork[i] > st->fd_work_max) st->fd_work_max = hwork[i];
     }
-    std::vector<ull> ps_h(2 * (size_t)nparts);
+    std::vector<ull> ps_h((size_t)WFD_PSTAT * nparts);
     CK(cudaMemcpy(ps_h.data(), pstat, ps_h.size() * 8, cudaMemcpyDeviceToHost));
     for (uint32_t i = 0; i < nparts; i++) {
-      st->fd_part_steps_max = std::max<uint64_t>(st->fd_part_steps_max, ps_h[2 * i]);
-      st->fd_part_cycles_max = std::max<uint64_t>(st->fd_part_cycles_max, ps_h[2 * i + 1]);
+      st->fd_part_steps_max = std::max<uint64_t>(st->fd_part_steps_max, ps_h[(size_t)WFD_PSTAT * i]);
+      st->fd_part_cycles_max = std::max<uint64_t>(st->fd_part_cycles_max, ps_h[(size_t)WFD_PSTAT * i + 1]);
     }
     st->bytes_count += 4 * hcc[0] + 12 * hcc[1] + 16 * hcc[2];
     st->bytes_peel += 8 * hw[0] + 16 * hw[1] + 8 * front_total;

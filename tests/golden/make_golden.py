@@ -4,8 +4,8 @@ For each full-size workload this records a hash of the generated graph (so a
 drift in the generator is detected), then runs the oracle's bottom-up peeling
 (Alg. 2) and stores a SHA-256 of the resulting uint64 tip numbers together
 with summary values and a fixed sample of (index, value) pairs.  Only
-``oracle`` and ``bigraph_gen`` are used.  Run once (it takes tens of
-minutes of CPU time); the GPU tests compare against the stored files.
+``oracle`` and ``bigraph_gen`` are used.  Run once (the tip jobs take tens
+of minutes of CPU time, the full-size wing job hours); the GPU tests compare against the stored files.
 
     python tests/golden/make_golden.py [name ...]
 """
@@ -15,6 +15,7 @@ import hashlib
 import json
 import multiprocessing as mp
 import os
+import platform
 import sys
 import time
 
@@ -30,6 +31,11 @@ JOBS = {
     "tip_chunglu_1m_200k_20m_V": ("chunglu_1m_200k_20m", "V"),
     "tip_chunglu_5m_1m_60m_U": ("chunglu_5m_1m_60m", "U"),
     "tip_batch_4096_U": ("batch", "U"),
+    # wing numbers (side "E": every edge) of the planted 500k x 100k graph,
+    # and of the same recipe on a 1M-edge Chung-Lu base with all 200 planted
+    # bicliques kept
+    "wing_chunglu_500k_100k_5m_planted": ("chunglu_500k_100k_5m_planted", "E"),
+    "wing_chunglu_500k_100k_1m_planted": ("chunglu_500k_100k_1m_planted", "E"),
 }
 BATCH_N, BATCH_SEED0 = 4096, 1000
 
@@ -68,10 +74,11 @@ def run(name: str) -> dict:
                "per_graph_sha256": [hashlib.sha256(t.tobytes()).hexdigest()[:16] for t in thetas]}
     else:
         g = gen.make(workload)
-        th = oracle.tip(g, side).astype(np.uint64)
+        th = (oracle.wing(g) if side == "E" else oracle.tip(g, side)).astype(np.uint64)
         rec = {"graph_sha256": graph_sha(g), "theta_sha256": hashlib.sha256(th.tobytes()).hexdigest(),
                "n": int(th.size), "max": int(th.max()), "sum": int(th.sum(dtype=np.uint64)), "samples": samples(th)}
-    rec.update({"job": name, "workload": workload, "side": side, "oracle": "bottom-up peeling (Alg. 2), oracle/oracle.c",
+    rec.update({"job": name, "workload": workload, "side": side, "oracle": "bottom-up peeling (Alg. 2), oracle/oracle.c", "host_cores_used": 1,
+                "host": platform.machine(),
                 "cpu_seconds": round(time.time() - t0, 1)})
     with open(os.path.join(HERE, name + ".json"), "w") as f:
         json.dump(rec, f, indent=1)

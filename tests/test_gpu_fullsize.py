@@ -120,10 +120,30 @@ def test_batch_4096_tip_p150(pbng):
     assert h.hexdigest() == gd["theta_sha256"]
 
 
+def test_chunglu_500k_100k_1m_planted_wing_p100(pbng):
+    """The planted recipe with all 200 bicliques on a 1M-edge Chung-Lu base:
+    every wing number equals the oracle's complete bottom-up peeling."""
+    gd = golden("wing_chunglu_500k_100k_1m_planted")
+    g = graph("chunglu_500k_100k_1m_planted")
+    assert gsha(g) == gd["graph_sha256"]
+    dg = pbng.to_device(g)
+    theta = pbng.as_u64(pbng.wing_decompose(dg, P=100))
+    for i, v in gd["samples"]:
+        assert int(theta[i]) == v
+    assert hashlib.sha256(theta.tobytes()).hexdigest() == gd["theta_sha256"]
+
+
 def test_chunglu_500k_100k_5m_planted_wing_p100(pbng):
     g = graph("chunglu_500k_100k_5m_planted")
     dg = pbng.to_device(g)
     theta = pbng.as_u64(pbng.wing_decompose(dg, P=100))
+    p = os.path.join(GOLDEN, "wing_chunglu_500k_100k_5m_planted.json")
+    if os.path.exists(p):  # the oracle's complete peeling: bit-exact over every edge
+        gd = golden("wing_chunglu_500k_100k_5m_planted")
+        assert gsha(g) == gd["graph_sha256"]
+        for i, v in gd["samples"]:
+            assert int(theta[i]) == v
+        assert hashlib.sha256(theta.tobytes()).hexdigest() == gd["theta_sha256"]
     ce = pbng.as_u64(pbng.count(dg, vertices=False, edges=True)[2])
     assert (theta <= ce).all()
     # any bounds give the same numbers (Th. 2): a different partition count

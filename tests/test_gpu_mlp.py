@@ -113,8 +113,29 @@ def test_learned_bounds_give_identical_tip_numbers(pbng, name):
     used = np.zeros(200, dtype=np.uint64)
     th, st = pbng.tip_decompose(dg, "U", P=200, mlp=mlp, with_stats=True, bounds_out=used)
     assert np.array_equal(pbng.as_u64(th), oracle.tip(g, "U"))
-    b = used[:st["parts_used"] - 1]
+    b = used[:np.count_nonzero(used)]
+    assert b.size in (st["parts_used"] - 1, st["parts_used"])
     assert (np.diff(b.astype(np.float64)) > 0).all()
+
+
+def test_propose_bounds_learned(pbng):
+    """pbng_propose_bounds with the learned proposer: the bounds the coarse
+    phase uses (learned proposals judged by the estimator) reproduce the
+    oracle's tip numbers when passed back explicitly."""
+    import torch
+    from paper_2110_12511_gb300 import learned
+    g = gen.make("chunglu_20k_4k_200k")
+    dg = pbng.to_device(g)
+    mlp = learned.load(WEIGHTS) if os.path.exists(WEIGHTS) else (
+        torch.as_tensor(learned.init_params(199, 1), device="cuda"), 128, 199)
+    b = pbng.propose_bounds(dg, "U", P=200, mlp=mlp)
+    inner = b[1:][b[1:] != np.iinfo(np.uint64).max]
+    used = np.zeros(201, dtype=np.uint64)
+    _, st = pbng.tip_decompose(dg, "U", P=200, mlp=mlp, with_stats=True, bounds_out=used)
+    assert inner.size in (st["parts_used"] - 1, st["parts_used"])
+    assert np.array_equal(used[:inner.size], inner) and not used[inner.size:].any()
+    th = pbng.tip_decompose(dg, "U", P=200, bounds=inner)
+    assert np.array_equal(pbng.as_u64(th), oracle.tip(g, "U"))
 
 
 def test_learned_bounds_gain_on_heldout_graph(pbng):

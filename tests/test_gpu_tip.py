@@ -297,3 +297,61 @@ def test_autotuner_choice_gives_identical_numbers(pbng, tmp_path):
     gs = [gen.batch_graph(1000 + i, scale=0.05) for i in range(8)]
     size, tb = at.tune_batch([pbng.to_device(g) for g in gs], "U", P=20, sizes=(2, 8), cfg=cfg)
     assert size in (2, 8) and len(tb) == 2
+
+
+def recount_bound(g, side):
+    """Smallest first bound whose active set (every vertex with initial count
+    below it) has more wedges than the counting bound sum_e min(d_u, d_v):
+    the round re-counts the remaining vertices instead of peeling (Sec. 5.1)."""
+    h = g if side == "U" else g.swapped()
+    du = np.diff(h.u_off).astype(np.int64)
+    dv = np.bincount(h.u_adj, minlength=h.nv).astype(np.int64)
+    eu = np.repeat(np.arange(h.nu), du)
+    wbound = int(np.minimum(du[eu], dv[h.u_adj]).sum())
+    W = np.bincount(eu, weights=dv[h.u_adj], minlength=h.nu)
+    cnt = oracle.vertex_counts(g, side)
+    order = np.argsort(cnt, kind="stable")
+    k = int(np.searchsorted(np.cumsum(W[order]), wbound, side="right"))
+    assert k < h.nu, "no first round exceeds the counting bound on this graph"
+    return int(cnt[order[k]]) + 1, wbound
+
+
+@pytest.mark.parametrize("side", ["U", "V"])
+def test_tip_recount_branch_runs(pbng, side):
+    """Sec. 5.1: the first round's active vertices have more wedges than the
+    counting bound, so the round re-counts the remaining vertices; the tip
+    numbers still equal the oracle's, and without re-count nothing is re-counted."""
+    name = "chunglu_20k_4k_200k"
+    g = GRAPHS[name]
+    dg = pbng.to_device(g)
+    b0, wbound = recount_bound(g, side)
+    bounds = np.array([b0, 2 * b0, 4 * b0], dtype=np.uint64)
+    got, st = pbng.tip_decompose(dg, side, P=5, bounds=bounds, recount=True, with_stats=True)
+    assert st["wedge_bound"] == wbound
+    assert st["recounts"] > 0
+    assert np.array_equal(pbng.as_u64(got), oracle_tip(name, side))
+    got2, st2 = pbng.tip_decompose(dg, side, P=5, bounds=bounds, recount=False, with_stats=True)
+    assert st2["recounts"] == 0
+    assert np.array_equal(pbng.as_u64(got2), oracle_tip(name, side))
+    assert st["wedges_cd"] < st2["wedges_cd"]  # the re-count replaced a heavier peel
+
+
+@pytest.mark.parametrize("side", ["U", "V"])
+@pytest.mark.parametrize("P", [1, 8, 40])
+def test_propose_bounds_reproduce_the_ranges(pbng, side, P):
+    """pbng_propose_bounds returns theta(1..P+1) of the coarse phase
+    (Sec. 3.1.3); fed back as explicit bounds they give the same ranges and
+    the oracle's tip numbers (Sec. 4.1 Th. 2)."""
+    name = "chunglu_20k_4k_200k"
+    dg = pbng.to_device(GRAPHS[name])
+    b = pbng.propose_bounds(dg, side, P=P)
+    assert b.size == P + 1 and b[0] == 0 and b[-1] == np.iinfo(np.uint64).max
+    inner = b[1:][b[1:] != np.iinfo(np.uint64).max]
+    assert np.all(np.diff(inner.astype(np.float64)) > 0)
+    used = np.zeros(P + 1, dtype=np.uint64)
+    th, st = pbng.tip_decompose(dg, side, P=P, with_stats=True, bounds_out=used)
+    assert inner.size in (st["parts_used"] - 1, st["parts_used"])
+    assert np.array_equal(used[:inner.size], inner) and not used[inner.size:].any()
+    th2, st2 = pbng.tip_decompose(dg, side, P=P, bounds=inner, with_stats=True)
+    assert np.array_equal(pbng.as_u64(th2), oracle_tip(name, side))
+    assert st2["parts_used"] == st["parts_used"]

@@ -54,10 +54,38 @@ def test_wing_matches_oracle(pbng, name):
     dg = pbng.to_device(GRAPHS[name])
     got, st = pbng.wing_decompose(dg, P=16, with_stats=True)
     assert np.array_equal(pbng.as_u64(got), oracle_wing(name))
-    if GRAPHS[name].m:
-        # Prop. 1-2: sum over blooms of C(k,2) butterflies; each edge's count is
-        # the sum over its blooms of (k-1): the index has 2 links per pair
-        assert st["links"] % 2 == 0
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_be_index_properties(pbng, name):
+    """Sec. 2.3 Property 1-2 on the BE-Index the wing path builds: every
+    butterfly lies in exactly one maximal priority bloom, which holds C(k_B, 2)
+    of them, and an edge of bloom B lies in k_B - 1 of B's butterflies; so the
+    per-edge sums over blooms equal the oracle's edge counts and the sum over
+    blooms equals the oracle's total (sum of edge counts / 4 = sum of U-vertex
+    counts / 2)."""
+    g = GRAPHS[name]
+    dg = pbng.to_device(g)
+    (per_edge, total), st = pbng.be_index_sums(dg, with_stats=True)
+    ce = oracle.edge_counts(g)
+    assert np.array_equal(pbng.as_u64(per_edge), ce)
+    butterflies = int(ce.sum(dtype=np.uint64)) // 4
+    assert total == butterflies
+    assert 2 * total == int(oracle.vertex_counts(g, "U").sum(dtype=np.uint64))
+    # and the decomposition runs on an index of the same size
+    _, sw = pbng.wing_decompose(dg, P=16, with_stats=True)
+    assert (st["links"], st["blooms"]) == (sw["links"], sw["blooms"])
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("cmin", [1, 0xFFFFFFFF])
+def test_wing_cluster_fine_phase(pbng, name, cmin):
+    """Fine phase with every partition peeled by a thread-block cluster
+    (cmin = 1) or by single blocks only: the oracle's numbers either way."""
+    dg = pbng.to_device(GRAPHS[name])
+    for P in (1, 16):
+        got = pbng.wing_decompose(dg, P=P, schedule={"fd_cluster_min": cmin})
+        assert np.array_equal(pbng.as_u64(got), oracle_wing(name))
 
 
 @pytest.mark.parametrize("P", [1, 2, 7, 100, 10 ** 6])
