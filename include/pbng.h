@@ -98,7 +98,17 @@ typedef struct pbng_opts {
                                tip: vertices) is peeled by a cluster of thread blocks sharing its
                                step state instead of one block; 0 = default (32768), 0xffffffff =
                                never; results are identical */
+  uint32_t count_scratch;   /* counting (Alg. 1) scratch counters of a start with more than 256 wedges:
+                               PBNG_SCRATCH_AUTO (0, default: dense shared counters for the 16384
+                               highest-priority starts, shared hashes up to 4096 wedges, then dense
+                               counters over all vertices in global memory), PBNG_SCRATCH_HASH (no
+                               dense shared class), PBNG_SCRATCH_DENSE (dense shared counters only:
+                               16-bit, over chunks of 32768 labels beyond the first 16384),
+                               PBNG_SCRATCH_DENSE32 (the same with 32-bit counters); results are
+                               identical */
 } pbng_opts;
+
+enum { PBNG_SCRATCH_AUTO = 0, PBNG_SCRATCH_HASH = 1, PBNG_SCRATCH_DENSE = 2, PBNG_SCRATCH_DENSE32 = 3 };
 
 typedef struct pbng_stats {
   uint64_t wedges_count;   /* wedges traversed by the initial count (Alg. 1) */

@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
                 ("mlp_params", ctypes.c_void_p), ("mlp_hidden", ctypes.c_uint32), ("mlp_out", ctypes.c_uint32),
                 ("bounds_out", ctypes.c_void_p), ("n_bounds_out", ctypes.c_uint32),
                 ("bucket_shift", ctypes.c_uint32), ("warp_max_w", ctypes.c_uint32),
-                ("group_max_w", ctypes.c_uint32), ("item_w", ctypes.c_uint32), ("fd_cluster_min", ctypes.c_uint32)]
+                ("group_max_w", ctypes.c_uint32), ("item_w", ctypes.c_uint32), ("fd_cluster_min", ctypes.c_uint32),
+                ("count_scratch", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -156,7 +157,8 @@ def to_device(g, device="cuda") -> DeviceGraph:
     return DeviceGraph(int(g.nu), int(g.nv), off, adj)
 
 
-SCHEDULE_KEYS = ("bucket_shift", "warp_max_w", "group_max_w", "item_w", "fd_cluster_min")
+SCHEDULE_KEYS = ("bucket_shift", "warp_max_w", "group_max_w", "item_w", "fd_cluster_min", "count_scratch")
+SCRATCH_AUTO, SCRATCH_HASH, SCRATCH_DENSE, SCRATCH_DENSE32 = 0, 1, 2, 3
 
 
 def _opts(stream=None, bounds=None, recount=True, compact=True, mem=MEM_DEVICE, graph_rounds=False, keep=None,
@@ -197,15 +199,16 @@ def _opts(stream=None, bounds=None, recount=True, compact=True, mem=MEM_DEVICE, 
     return o
 
 
-def count(dg: DeviceGraph, vertices=True, edges=False, stream=None, with_stats=False):
-    """Per-vertex (U and V) and per-edge butterfly counts (Alg. 1)."""
+def count(dg: DeviceGraph, vertices=True, edges=False, stream=None, with_stats=False, scratch=0):
+    """Per-vertex (U and V) and per-edge butterfly counts (Alg. 1); scratch:
+    the counters of the heavier starts (SCRATCH_*)."""
     import torch
     dev = dg.u_off.device
     cu = torch.empty(max(dg.nu, 1), dtype=torch.int64, device=dev) if vertices else None
     cv = torch.empty(max(dg.nv, 1), dtype=torch.int64, device=dev) if vertices else None
     ce = torch.empty(max(dg.m, 1), dtype=torch.int64, device=dev) if edges else None
     st = Stats()
-    o = _opts(stream)
+    o = _opts(stream, schedule={"count_scratch": scratch})
     g = dg.c_struct()
     rc = lib().pbng_count(ctypes.byref(g), cu.data_ptr() if cu is not None else None,
                           cv.data_ptr() if cv is not None else None, ce.data_ptr() if ce is not None else None,

@@ -112,6 +112,8 @@ TipParams tip_params(uint32_t P, const pbng_opts &o) {
     p.item_w = o.item_w;
   }
   p.fd_cluster_min = o.fd_cluster_min ? o.fd_cluster_min : 32768u;
+  if (o.count_scratch > PBNG_SCRATCH_DENSE32) fail(PBNG_EINVAL, "unknown count_scratch %u", o.count_scratch);
+  p.count_scratch = (int)o.count_scratch;
   p.timeout_ns = o.timeout_ns ? o.timeout_ns : 10000000000ull;
   p.mlp_params = o.mlp_params;
   p.mlp_hidden = o.mlp_hidden;
@@ -221,10 +223,12 @@ int pbng_count(const pbng_bigraph *g, uint64_t *out_u, uint64_t *out_v, uint64_t
     uint64_t *cnt = a.zeros<uint64_t>((size_t)G.n + 1);
     if (be.dev && G.m) CK(cudaMemsetAsync(be.dev, 0, (size_t)G.m * 8, a.st));
     uint64_t *wd = a.zeros<uint64_t>(3);
+    if (o.count_scratch > PBNG_SCRATCH_DENSE32) fail(PBNG_EINVAL, "unknown count_scratch %u", o.count_scratch);
     CountOut co;
     co.cnt_lab = cnt;
     co.cnt_e = be.dev;
     co.wedges = wd;
+    co.scratch = (int)o.count_scratch;
     count_butterflies(a, G, co);
     if (bu.dev && G.nu)
       k_gather_lab<<<grid_for(G.nu, 256, 16 * num_sms()), 256, 0, a.st>>>((unsigned long long *)cnt, G.g2lab, 0, G.nu, bu.dev);

@@ -9,6 +9,10 @@
 // drops below hi during an update joins the candidates (detected from the
 // atomic's old value, so exactly once).  A new window is chosen when the
 // candidates run out.  Peeling order and recorded numbers are unchanged.
+// The window size adapts: a window of C candidates costs one scan of the n
+// remaining entities plus two scans of C per step, so with r steps per
+// entity (measured on the previous window) about sqrt(1.5 n / r) entities
+// per window balance the two (bounded by the caller's cap).
 // An entity that joined the candidates also stays in the non-candidate list;
 // it is peeled through the candidates, and later windows drop it.
 //
@@ -26,7 +30,8 @@
 
 namespace pbng {
 
-constexpr uint32_t WIN_CAP = 4096;
+constexpr uint32_t WIN_CAP = 4096;    // largest window of a one-block team
+constexpr uint32_t WIN_CAP_BIG = 65536;  // and of a cluster team (per cluster)
 
 struct FDLists {
   uint32_t *a[2];  // remaining non-candidates (double buffer)
@@ -40,6 +45,7 @@ struct FDShared {
   uint32_t hist[65];
   uint32_t p;        // partition being peeled
   uint32_t nt, ncq;  // per-step work lists of the kernels (touched groups, compaction queue)
+  uint32_t wn, ws;   // entities of the current window when it was chosen, steps taken since
 };
 
 // per-block scratch of a team's minimum reduction
@@ -173,10 +179,13 @@ __device__ uint32_t fd_select(const Team &T, const FDLists &L, unsigned long lon
     }
     T.sync();
     if (T.leader()) {
+      // window size from the previous window's steps per entity (1 for the first)
+      const float r = S->wn ? fmaxf((float)S->ws, 1.0f) / (float)S->wn : 1.0f;
+      const uint32_t w = (uint32_t)fminf((float)cap, fmaxf(64.0f, sqrtf(1.5f * (float)na / r)));
       uint32_t cum = 0, b = 0;
       for (uint32_t i = 0; i < 65; i++) {
         uint32_t h = *(volatile uint32_t *)&S->hist[i];
-        if (i > 0 && cum + h > cap) break;
+        if (i > 0 && cum + h > w) break;
         cum += h;
         b = i;
       }
@@ -202,6 +211,8 @@ __device__ uint32_t fd_select(const Team &T, const FDLists &L, unsigned long lon
     if (T.leader()) {
       S->na = *(volatile uint32_t *)&S->nn;
       S->pa ^= 1;
+      S->wn = *(volatile uint32_t *)&S->nc;
+      S->ws = 0;
     }
     T.sync();
   }
@@ -211,6 +222,7 @@ __device__ uint32_t fd_select(const Team &T, const FDLists &L, unsigned long lon
   for (uint32_t j = T.tid(); j < nc; j += nthr) mn = min(mn, ldt(&sup[ldt(&lc[j])]));
   mn = T.reduce_min(mn);
   if (T.leader()) {
+    S->ws++;
     S->level = max(*(volatile unsigned long long *)&S->level, mn);
     S->nf = 0;
     S->nn = 0;

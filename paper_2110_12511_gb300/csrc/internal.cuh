@@ -99,6 +99,45 @@ static inline unsigned grid_for(size_t n, unsigned threads, unsigned cap = 1u <<
   return (unsigned)g;
 }
 
+// ------------------------------------------------------ cluster launches
+// Thread-block clusters for the fine phase's heavy partitions: the cluster
+// size (16 blocks where the device can hold such clusters for `kernel`, else
+// 8, else 1 = none) and how many run at once (at most half of the SMs, so
+// that one-block teams keep the rest).  Cached per kernel.
+struct FDClusterShape {
+  uint32_t size = 1, max_clusters = 0;
+};
+FDClusterShape fd_cluster_shape(const void *kernel, int threads, size_t smem);
+
+// launch `kernel` as nclusters clusters of csize blocks on stream st
+template <class... Args>
+cudaError_t launch_cluster(const void *kernel, uint32_t nclusters, uint32_t csize, int threads, size_t smem,
+                           cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nclusters * csize);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  void *ptrs[] = {(void *)&args...};
+  return cudaLaunchKernelExC(&cfg, kernel, ptrs);
+}
+
+// A side stream forked from `main` (when on): work issued on st runs
+// concurrently with main's, and main waits for it when this goes out of scope.
+struct SideLaunch {
+  cudaStream_t main = nullptr, st = nullptr;
+  cudaEvent_t ev = nullptr;
+  SideLaunch(cudaStream_t m, bool on);
+  ~SideLaunch();
+};
+
 // ------------------------------------------------------------------ graph
 // Internal graph in 32-bit CSR form plus the degree-priority labelled
 // adjacency used by Alg. 1.  Edge id = position in the U-side CSR.
@@ -132,6 +171,7 @@ struct CountOut {
   uint64_t *wedges = nullptr;    // optional device counters [3]: wedges, expansions, updates
   uint64_t *be_nb = nullptr;     // optional per-label BE-Index sizes: blooms started at the label
   uint64_t *be_np = nullptr;     // and their twin pairs (caller zeroes both)
+  int scratch = PBNG_SCRATCH_AUTO;  // scratch counters of the heavier starts (pbng_opts.count_scratch)
 };
 // Alg. 1 over the labelled adjacency (all starts).
 void count_butterflies(Arena &a, const Graph &G, const CountOut &o);
@@ -163,6 +203,7 @@ struct TipParams {
   uint32_t bucket_shift;  // 0 = automatic
   uint32_t warp_max_w, group_max_w, item_w;  // coarse-peel schedule, 0 = default
   uint32_t fd_cluster_min;                   // fine phase: smallest partition for a cluster team
+  int count_scratch;                         // counting: scratch counters (PBNG_SCRATCH_*)
   uint64_t timeout_ns;
   const float *mlp_params;  // learned bounds (bounds_mode == PBNG_BOUNDS_LEARNED)
   uint32_t mlp_hidden, mlp_out;
@@ -196,7 +237,7 @@ struct BEIndex {
   uint32_t *k0 = nullptr, *boff = nullptr, *pe1 = nullptr, *pe2 = nullptr, *pbloom = nullptr;
   uint32_t *eoff = nullptr, *elink = nullptr;
 };
-void be_index_build(Arena &a, const Graph &G, unsigned long long *sup_e, uint64_t *cctr, BEIndex &I);
+void be_index_build(Arena &a, const Graph &G, unsigned long long *sup_e, uint64_t *cctr, BEIndex &I, int scratch);
 // out_e[e] = sum over the blooms B of e of (k_B - 1); *total = sum over blooms of C(k_B, 2)
 void be_index_sums(Arena &a, const Graph &G, uint64_t *out_e, uint64_t *total, pbng_stats *st);
 void wing_decompose(Arena &a, Graph &G, const TipParams &p, uint64_t *theta_out, pbng_stats *st);

@@ -4,6 +4,10 @@
 #include <cstdio>
 #include <cstring>
 
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace pbng {
@@ -336,6 +340,52 @@ uint32_t reduce_max_u32(Arena &a, const uint32_t *in, size_t n) {
   uint32_t r = fetch(a, (const uint32_t *)d);
   a.free(d);
   return r;
+}
+
+FDClusterShape fd_cluster_shape(const void *kernel, int threads, size_t smem) {
+  static std::vector<std::pair<const void *, FDClusterShape>> cache;
+  for (auto &c : cache)
+    if (c.first == kernel) return c.second;
+  FDClusterShape fc;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
+  for (uint32_t cs : {16u, 8u}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) == cudaSuccess && n > 0) {
+      fc.size = cs;
+      fc.max_clusters = std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)n, (uint32_t)num_sms() / (2 * cs)));
+      break;
+    }
+    cudaGetLastError();
+  }
+  cache.push_back({kernel, fc});
+  return fc;
+}
+
+SideLaunch::SideLaunch(cudaStream_t m, bool on) : main(m) {
+  if (!on) return;
+  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(ev, main));
+  CK(cudaStreamWaitEvent(st, ev, 0));
+}
+
+SideLaunch::~SideLaunch() {
+  if (!st) return;
+  // (no throwing here: a failure shows up in the caller's next check)
+  if (cudaEventRecord(ev, st) == cudaSuccess) cudaStreamWaitEvent(main, ev, 0);
+  cudaEventDestroy(ev);
+  cudaStreamDestroy(st);
 }
 
 }  // namespace pbng

@@ -36,6 +36,8 @@ namespace {
 enum : uint8_t { ST_ALIVE = 0, ST_ACTIVE = 1, ST_PEELED = 2 };
 
 constexpr uint32_t PW_MAXW = 256, PW_CAP = 512;  // fine phase: warp-per-vertex shared hash
+constexpr uint32_t FEW_VERTICES = 8, WARP_FEW_W = 192;  // fine phase: few peeled vertices -> team-wide above this
+constexpr uint32_t HW_KEEP = 4;  // fine phase, team path: wedges a thread keeps between its two passes
 constexpr uint32_t QW_MAXW = 512, QW_CAP = 1024;  // coarse peel: warp-per-vertex shared hash
 constexpr uint32_t QG_MAXW = 2048, QG_CAP = 4096; // coarse peel: 256-thread group per vertex
 constexpr int QGT = 256;                          // threads of a group
@@ -77,42 +79,6 @@ struct PMid {
   uint32_t lo[N];
   uint32_t len[N];
   uint32_t pre[N + 1];
-};
-
-// NT threads of a block (warps base/32 .. ) synchronised by a named barrier
-template <int NT>
-struct SubGrp {
-  static constexpr int N = NT;
-  int base, bar;
-  uint32_t *ws;  // NT/32 + 2 words of shared scratch
-  __device__ __forceinline__ int rank() const { return (int)threadIdx.x - base; }
-  __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(NT) : "memory"); }
-  __device__ __forceinline__ uint32_t scan(uint32_t x, uint32_t *pre) const {
-    int r = rank(), l = r & 31, w = r >> 5;
-    uint32_t inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (l >= o) inc += y;
-    }
-    if (l == 31) ws[w] = inc;
-    sync();
-    if (w == 0) {
-      uint32_t s = l < NT / 32 ? ws[l] : 0u, si = s;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, si, o);
-        if (l >= o) si += y;
-      }
-      if (l < NT / 32) ws[l] = si - s;
-      if (l == NT / 32 - 1) ws[NT / 32] = si;
-    }
-    sync();
-    pre[r] = inc - x + ws[w];
-    if (r == 0) pre[NT] = ws[NT / 32];
-    sync();
-    return pre[NT];
-  }
 };
 
 // support(x') -= dec.  No return value is needed (the next active set is
@@ -220,7 +186,7 @@ __global__ void __launch_bounds__(2 * QGT) k_peel_group(PeelArgs A, const uint64
   uint32_t *key = (uint32_t *)base, *val = key + QG_CAP;
   PMid<QGT> &mb = *(PMid<QGT> *)(base + QG_CAP * 8);
   uint32_t *ws = (uint32_t *)(base + QG_CAP * 8 + sizeof(PMid<QGT>));
-  SubGrp<QGT> g{sub * QGT, 1 + sub, ws};
+  SubGrp<QGT> g{sub * QGT, 1 + sub, ws, nullptr};
   for (uint32_t i = g.rank(); i < QG_CAP; i += QGT) key[i] = EMPTY_KEY, val[i] = 0;
   g.sync();
   uint64_t nup = 0;
@@ -879,9 +845,11 @@ struct FDArgs {
   ull *pstat;  // per partition: steps, SM cycles
   const uint32_t *seg_lo, *seg_len;  // per X-side edge: slice of (y, part(x)) in fd_adj
   const uint32_t *w_fd;              // per vertex: wedges in its partition's subgraph
+  const uint32_t *seg_n;             // per vertex: its non-empty slices (from its first edge position)
 };
 
 constexpr int FT = 512, FW = FT / 32;
+constexpr int TFD_PSTAT = 7;  // per-partition statistics of the fine phase
 
 template <int N>
 struct FMid {
@@ -911,23 +879,34 @@ __device__ __forceinline__ uint32_t fd_load(const FDArgs &A, uint32_t p, uint32_
   return g.scan(len, mb.pre);
 }
 
-// once per call: every X-side edge (x, y) gets the slice of y's partitioned
-// list that holds partition part(x), and every x its wedge count in G_part(x)
-__global__ void k_fd_segs(FDArgs A, uint32_t nx, const uint32_t *part, uint32_t *seg_lo, uint32_t *seg_len, uint32_t *w_fd) {
+// once per call: every x gets the non-empty slices of its neighbours'
+// partitioned lists that hold partition part(x) - compacted to the front of
+// its own edge range, seg_n[x] of them - and its wedge count in G_part(x)
+// (a neighbour with no vertex of the partition costs nothing later)
+__global__ void k_fd_segs(FDArgs A, uint32_t nx, const uint32_t *part, uint32_t *seg_lo, uint32_t *seg_len, uint32_t *w_fd,
+                          uint32_t *seg_n) {
   int lane = threadIdx.x & 31;
   size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
   for (size_t x = gw; x < nx; x += nw) {
-    uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo, p = part[x], W = 0;
-    for (uint32_t k = lane; k < xd; k += 32) {
-      uint32_t lo, len;
-      fd_seg(A, A.p_adj[xo + k], p, lo, len);
-      seg_lo[xo + k] = lo;
-      seg_len[xo + k] = len;
+    uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo, p = part[x], W = 0, out = 0;
+    for (uint32_t k0 = 0; k0 < xd; k0 += 32) {
+      uint32_t lo = 0, len = 0;
+      if (k0 + lane < xd) fd_seg(A, A.p_adj[xo + k0 + lane], p, lo, len);
+      const unsigned b = __ballot_sync(0xffffffffu, len > 0);
+      if (len) {
+        const uint32_t at = xo + out + __popc(b & ((1u << lane) - 1u));
+        seg_lo[at] = lo;
+        seg_len[at] = len;
+      }
+      out += __popc(b);
       W += len;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
-    if (lane == 0) w_fd[x] = W;
+    if (lane == 0) {
+      w_fd[x] = W;
+      seg_n[x] = out;
+    }
   }
 }
 
@@ -935,100 +914,134 @@ __global__ void k_fd_segs(FDArgs A, uint32_t nx, const uint32_t *part, uint32_t 
 // are short, so one lane per wedge beats whole-warp chunks here)
 template <class Grp, int N, class F>
 __device__ __forceinline__ void fd_walk(const FDArgs &A, const Grp &g, const FMid<N> &mb, uint32_t T, F &&f) {
-  for (uint32_t w = g.rank(); w < T; w += N) {
+  uint32_t w = g.rank();
+  for (; w + N < T; w += 2 * N) {  // two wedges in flight
+    int i0 = seg_of(mb.pre, N, w), i1 = seg_of(mb.pre, N, w + N);
+    uint32_t a0 = A.fd_adj[mb.lo[i0] + (w - mb.pre[i0])], a1 = A.fd_adj[mb.lo[i1] + (w + N - mb.pre[i1])];
+    f(a0);
+    f(a1);
+  }
+  if (w < T) {
     int i = seg_of(mb.pre, N, w);
     f(A.fd_adj[mb.lo[i] + (w - mb.pre[i])]);
   }
 }
 
-__device__ __forceinline__ uint8_t ld_state(const uint8_t *s) { return *(volatile const uint8_t *)s; }
+// Dense counters of the partition being peeled, indexed by the local index
+// of a vertex: in the team's shared memory (a cluster spreads them over its
+// blocks, index loc in block loc mod size at loc / size), or in global memory
+// when the partition is larger than that.
+struct FDCounters {
+  uint32_t *dense;   // this block's shared array (P_DENSE entries)
+  uint32_t *global;  // the partition's global array, or null
+  uint32_t lg;       // log2 of the team's blocks
+  template <bool CL>
+  __device__ __forceinline__ uint32_t *at(uint32_t loc) const {
+    if (global) return global + loc;
+    if (!CL) return dense + loc;
+    return cooperative_groups::this_cluster().map_shared_rank(dense, loc & ((1u << lg) - 1u)) + (loc >> lg);
+  }
+};
 
-__global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size_t dense_off) {
-  extern __shared__ __align__(16) uint8_t sm[];
-  __shared__ uint32_t s_p, s_fidx, s_nbig;
-  __shared__ FDShared S;
-  __shared__ uint32_t ws[FT / 32 + 2];
-  __shared__ ull ws64[FT / 32];
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Fine phase of the partitions handed out by A.queue / A.order (Sec. 3.1.2,
+// 3.2): bottom-up peeling of G_p from init, one partition at a time per team.
+// Each step: the selection (fd_select), then the updates of the peeled
+// vertices - a warp per vertex with few wedges in G_p (shared hash), the
+// whole team per heavy vertex (dense counters over the partition).  A step
+// after which nothing remains in the partition does no updates: they could
+// reach no remaining vertex.
+template <class Team>
+__device__ void tip_fd_run(const FDArgs &A, const Team &T, uint32_t cap, uint8_t *sm, size_t warp_bytes,
+                           FMid<FT> &bmb, uint32_t *dense, const BlockGrp<FT> &bg) {
+  constexpr bool CL = Team::kCluster;
+  FDShared *S = T.S;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t *wkey = (uint32_t *)(sm + warp * warp_bytes), *wval = wkey + PW_CAP;
   FMid<32> &wmb = *(FMid<32> *)(sm + warp * warp_bytes + PW_CAP * 8);
-  FMid<FT> &bmb = *(FMid<FT> *)(sm + FW * warp_bytes);
-  uint32_t *dense = (uint32_t *)(sm + dense_off);
   for (uint32_t i = lane; i < PW_CAP; i += 32) wkey[i] = EMPTY_KEY, wval[i] = 0;
   for (uint32_t i = threadIdx.x; i < P_DENSE; i += FT) dense[i] = 0;
-  __syncthreads();
+  const uint32_t nthr = T.nthr(), csize = nthr / FT;
+  uint32_t lg = 0;
+  while ((1u << lg) < csize) lg++;
+  const uint32_t rank = T.tid() / FT;
+  T.sync();
   WarpGrp wg;
-  BlockGrp<FT> bg{ws, ws64};
-  __shared__ TeamMin tmin;
-  BlockTeam T{&S, S.hist, &tmin};
   ull my_wedges = 0, my_updates = 0, my_steps = 0;
   for (;;) {
-    if (threadIdx.x == 0) {
+    if (T.leader()) {
       unsigned q = atomicAdd(A.queue, 1u);
-      s_p = q < A.nparts ? A.order[q] : 0xffffffffu;
+      S->p = q < A.nparts ? A.order[q] : 0xffffffffu;
     }
-    __syncthreads();
-    uint32_t p = s_p;
+    T.sync();
+    const uint32_t p = *(volatile uint32_t *)&S->p;
+    T.sync();  // every block has read p before it can change, or before the team exits
     if (p == 0xffffffffu) break;
-    uint32_t base = A.ps[p], np = A.ps[p + 1] - base;
+    const uint32_t base = A.ps[p], np = A.ps[p + 1] - base;
     uint32_t *lf = A.buf_f + base, *lbig = A.buf_big + base;
     FDLists L{{A.buf_a + base, A.buf_b + base}, {A.buf_c + base, A.buf_d + base}, lf};
-    bool smem_dense = np <= P_DENSE;
-    uint32_t *cnt = smem_dense ? dense : A.gcnt + base;
-    for (uint32_t j = threadIdx.x; j < np; j += FT) L.a[0][j] = A.xs[base + j];
-    if (threadIdx.x == 0) {
-      S.na = np;
-      S.nc = 0;
-      S.pa = 0;
-      S.pc = 0;
-      S.level = 0;
+    const FDCounters cnt{dense, np <= P_DENSE * csize ? nullptr : A.gcnt + base, lg};
+    for (uint32_t j = T.tid(); j < np; j += nthr) L.a[0][j] = A.xs[base + j];
+    if (T.leader()) {
+      S->na = np;
+      S->wn = 0;
+      S->ws = 0;
+      S->nc = 0;
+      S->pa = 0;
+      S->pc = 0;
+      S->level = 0;
     }
     long long t_part = clock64();
-    ull p_steps = 0;
-    __syncthreads();
-    while (S.na + S.nc > 0) {
+    ull p_steps = 0, cyc[3] = {0, 0, 0}, rescans = 0, nbigs = 0;
+    T.sync();
+    for (;;) {
+      if (*(volatile uint32_t *)&S->na + *(volatile uint32_t *)&S->nc == 0) break;
       p_steps++;
+      long long t0 = clock64();
+      rescans += *(volatile uint32_t *)&S->nc == 0;
       // every vertex at the running minimum is peeled with tip number = level
-      uint32_t nf = fd_select(T, L, A.sup, A.theta, A.state, ST_PEELED, ST_PEELED, WIN_CAP);
-      uint32_t *cand = L.c[S.pc];
-      const ull hi = S.hi;
-      if (threadIdx.x == 0) {
-        s_fidx = 0;
-        s_nbig = 0;
-      }
-      __syncthreads();
+      const uint32_t nf = fd_select(T, L, A.sup, A.theta, A.state, ST_PEELED, ST_PEELED, cap);
+      long long t1 = clock64();
+      cyc[0] += t1 - t0;
       my_steps++;
-      // warp-per-vertex updates for vertices with few wedges in G_p
+      // (uniform: crossings can only raise nc while something remains)
+      if (*(volatile uint32_t *)&S->na + *(volatile uint32_t *)&S->nc == 0) break;
+      uint32_t *cand = L.c[*(volatile uint32_t *)&S->pc];
+      const ull hi = *(volatile ull *)&S->hi;
+      // warp-per-vertex updates for vertices with few wedges in G_p (S->nt:
+      // next vertex, S->ncq: heavy vertices, both reset by the selection).
+      // When the step peels few vertices most warps would idle, so a vertex
+      // with more than WARP_FEW_W wedges goes to the team-wide path instead
+      const uint32_t big_w = nf <= FEW_VERTICES ? WARP_FEW_W : PW_MAXW;
       for (;;) {
         uint32_t k = 0;
-        if (lane == 0) k = atomicAdd(&s_fidx, 1u);
+        if (lane == 0) k = atomicAdd(&S->nt, 1u);
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k >= nf) break;
-        uint32_t x = lf[k];
-        uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
+        uint32_t x = ldt(&lf[k]);
+        uint32_t xo = A.p_off[x], xd = A.seg_n[x];
         uint32_t W = A.w_fd[x];
         if (W < 2) continue;
-        if (W > PW_MAXW) {
-          if (lane == 0) lbig[atomicAdd(&s_nbig, 1u)] = x;
+        if (W > big_w) {
+          if (lane == 0) lbig[atomicAdd(&S->ncq, 1u)] = x;
           continue;
         }
         my_wedges += lane == 0 ? W : 0;
-        uint32_t cap = pow2_at_least(max(2u * W, 32u));
-        SmemHash h{wkey, wval, cap - 1};
+        uint32_t capw = pow2_at_least(max(2u * W, 32u));
+        SmemHash h{wkey, wval, capw - 1};
         for (uint32_t b0 = 0; b0 < xd; b0 += 32) {
-          uint32_t T = fd_load(A, p, xo, xd, b0, wg, wmb);
-          fd_walk(A, wg, wmb, T, [&](uint32_t xp) {
-            if (ld_state(&A.state[xp]) == ST_ALIVE) h.inc(xp);
+          uint32_t Tw = fd_load(A, p, xo, xd, b0, wg, wmb);
+          fd_walk(A, wg, wmb, Tw, [&](uint32_t xp) {
+            if (ldt(&A.state[xp]) == ST_ALIVE) h.inc(xp);
           });
           __syncwarp();
         }
-        for (uint32_t i = lane; i < cap; i += 32) {
+        for (uint32_t i = lane; i < capw; i += 32) {
           uint32_t kk = wkey[i];
           if (kk != EMPTY_KEY) {
             uint32_t c = wval[i];
             if (c >= 2) {
               ull dec = choose2(c);
-              fd_crossing(&S.nc, cand, hi, kk, atomicAdd(&A.sup[kk], (ull)(0ull - dec)), dec);
+              fd_crossing(&S->nc, cand, hi, kk, atomicAdd(&A.sup[kk], (ull)(0ull - dec)), dec);
               my_updates++;
             }
             wkey[i] = EMPTY_KEY;
@@ -1037,39 +1050,110 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
         }
         __syncwarp();
       }
-      __syncthreads();
-      // block-per-vertex updates with dense counters over the partition
-      uint32_t nbig = s_nbig;
+      T.sync();
+      long long t2 = clock64();
+      cyc[1] += t2 - t1;
+      // heavy vertices: the whole team, dense counters over the partition;
+      // block r of the team walks neighbour chunks r, r + size, ...
+      const uint32_t nbig = *(volatile uint32_t *)&S->ncq;
+      nbigs += nbig;
       for (uint32_t bi = 0; bi < nbig; bi++) {
-        uint32_t x = lbig[bi];
-        uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo;
-        if (threadIdx.x == 0) my_wedges += A.w_fd[x];
-        for (uint32_t b0 = 0; b0 < xd; b0 += FT) {
-          uint32_t T = fd_load(A, p, xo, xd, b0, bg, bmb);
-          fd_walk(A, bg, bmb, T, [&](uint32_t xp) {
-            if (ld_state(&A.state[xp]) == ST_ALIVE) atomicAdd(&cnt[A.loc[xp]], 1u);
+        const uint32_t x = ldt(&lbig[bi]);
+        const uint32_t xo = A.p_off[x], xd = A.seg_n[x];
+        if (T.leader()) my_wedges += A.w_fd[x];
+        if (xd <= csize * FT) {
+          // one chunk of slices per block at most: a thread keeps the
+          // alive targets of its (at most HW_KEEP) wedges from the counting
+          // pass and takes their counts without a second walk
+          uint32_t keep[HW_KEEP], tgt[HW_KEEP];
+          const uint32_t b0 = rank * FT;
+          const uint32_t Tw = fd_load(A, p, xo, xd, min(b0, xd), bg, bmb);  // (empty past xd)
+          const bool cached = Tw <= HW_KEEP * FT;  // uniform in the block
+          if (cached) {
+#pragma unroll
+            for (uint32_t r = 0; r < HW_KEEP; r++) {  // loads of all kept wedges first
+              const uint32_t w = threadIdx.x + r * FT;
+              tgt[r] = EMPTY_KEY;
+              if (w < Tw) {
+                int i = seg_of(bmb.pre, FT, w);
+                tgt[r] = A.fd_adj[bmb.lo[i] + (w - bmb.pre[i])];
+              }
+            }
+#pragma unroll
+            for (uint32_t r = 0; r < HW_KEEP; r++) {
+              keep[r] = EMPTY_KEY;
+              if (tgt[r] != EMPTY_KEY && ldt(&A.state[tgt[r]]) == ST_ALIVE) {
+                keep[r] = A.loc[tgt[r]];
+                atomicAdd(cnt.at<CL>(keep[r]), 1u);
+              }
+            }
+          } else {
+            fd_walk(A, bg, bmb, Tw, [&](uint32_t xp) {
+              if (ldt(&A.state[xp]) == ST_ALIVE) atomicAdd(cnt.at<CL>(A.loc[xp]), 1u);
+            });
+          }
+          T.sync();
+          if (cached) {
+#pragma unroll
+            for (uint32_t r = 0; r < HW_KEEP; r++) {
+              const uint32_t l = keep[r];
+              if (l == EMPTY_KEY) continue;
+              uint32_t c = atomicExch(cnt.at<CL>(l), 0u);  // the first visitor takes the count
+              if (c >= 2) {
+                const uint32_t xp = tgt[r];
+                ull dec = choose2(c);
+                fd_crossing(&S->nc, cand, hi, xp, atomicAdd(&A.sup[xp], (ull)(0ull - dec)), dec);
+                my_updates++;
+              }
+            }
+          } else {
+            fd_walk(A, bg, bmb, Tw, [&](uint32_t xp) {
+              if (ldt(&A.state[xp]) != ST_ALIVE) return;
+              uint32_t c = atomicExch(cnt.at<CL>(A.loc[xp]), 0u);
+              if (c >= 2) {
+                ull dec = choose2(c);
+                fd_crossing(&S->nc, cand, hi, xp, atomicAdd(&A.sup[xp], (ull)(0ull - dec)), dec);
+                my_updates++;
+              }
+            });
+          }
+          __syncthreads();  // the chunk arrays are reused by the next vertex
+          T.sync();
+          continue;
+        }
+        for (uint32_t b0 = rank * FT; b0 < xd; b0 += csize * FT) {
+          uint32_t Tw = fd_load(A, p, xo, xd, b0, bg, bmb);
+          fd_walk(A, bg, bmb, Tw, [&](uint32_t xp) {
+            if (ldt(&A.state[xp]) == ST_ALIVE) atomicAdd(cnt.at<CL>(A.loc[xp]), 1u);
           });
           __syncthreads();
         }
-        for (uint32_t b0 = 0; b0 < xd; b0 += FT) {
-          uint32_t T = fd_load(A, p, xo, xd, b0, bg, bmb);
-          fd_walk(A, bg, bmb, T, [&](uint32_t xp) {
-            if (ld_state(&A.state[xp]) != ST_ALIVE) return;
-            uint32_t c = atomicExch(&cnt[A.loc[xp]], 0u);
+        T.sync();
+        for (uint32_t b0 = rank * FT; b0 < xd; b0 += csize * FT) {
+          uint32_t Tw = fd_load(A, p, xo, xd, b0, bg, bmb);
+          fd_walk(A, bg, bmb, Tw, [&](uint32_t xp) {
+            if (ldt(&A.state[xp]) != ST_ALIVE) return;
+            uint32_t c = atomicExch(cnt.at<CL>(A.loc[xp]), 0u);  // the first visitor takes the count
             if (c >= 2) {
               ull dec = choose2(c);
-              fd_crossing(&S.nc, cand, hi, xp, atomicAdd(&A.sup[xp], (ull)(0ull - dec)), dec);
+              fd_crossing(&S->nc, cand, hi, xp, atomicAdd(&A.sup[xp], (ull)(0ull - dec)), dec);
               my_updates++;
             }
           });
           __syncthreads();
         }
+        T.sync();
       }
-      __syncthreads();
+      T.sync();
+      cyc[2] += clock64() - t2;
     }
-    if (threadIdx.x == 0 && A.pstat) {
-      A.pstat[2 * p] = p_steps;
-      A.pstat[2 * p + 1] = (ull)(clock64() - t_part);
+    if (T.leader() && A.pstat) {  // steps, cycles; then select, warp path, team path, rescans, heavy vertices
+      ull *ps = A.pstat + (size_t)TFD_PSTAT * p;
+      ps[0] = p_steps;
+      ps[1] = (ull)(clock64() - t_part);
+      for (int k = 0; k < 3; k++) ps[2 + k] = cyc[k];
+      ps[5] = rescans;
+      ps[6] = nbigs;
     }
   }
   my_wedges = bg.sum64(my_wedges);
@@ -1077,8 +1161,35 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
   if (threadIdx.x == 0) {
     if (A.wedges) atomicAdd(A.wedges, my_wedges);
     if (A.updates) atomicAdd(A.updates, my_updates);
-    if (A.steps) atomicAdd(A.steps, my_steps);
   }
+  if (T.leader() && A.steps) atomicAdd(A.steps, my_steps);
+}
+
+// one block per partition
+__global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size_t dense_off, uint32_t cap) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ FDShared S;
+  __shared__ TeamMin tmin;
+  __shared__ uint32_t ws[FT / 32 + 2];
+  __shared__ ull ws64[FT / 32];
+  BlockGrp<FT> bg{ws, ws64};
+  BlockTeam T{&S, S.hist, &tmin};
+  tip_fd_run(A, T, cap, sm, warp_bytes, *(FMid<FT> *)(sm + FW * warp_bytes), (uint32_t *)(sm + dense_off), bg);
+}
+
+// one thread-block cluster per heavy partition (step state in the first
+// block's shared memory, dense counters spread over the blocks)
+__global__ void __launch_bounds__(FT) k_fd_tip_cluster(FDArgs A, size_t warp_bytes, size_t dense_off, uint32_t cap) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ FDShared S;
+  __shared__ TeamMin tmin;
+  __shared__ uint32_t lhist[65];
+  __shared__ uint32_t ws[FT / 32 + 2];
+  __shared__ ull ws64[FT / 32];
+  BlockGrp<FT> bg{ws, ws64};
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  ClusterTeam T{cl.map_shared_rank(&S, 0), lhist, &tmin, cl.block_rank(), cl.num_blocks()};
+  tip_fd_run(A, T, cap, sm, warp_bytes, *(FMid<FT> *)(sm + FW * warp_bytes), (uint32_t *)(sm + dense_off), bg);
 }
 
 size_t fd_warp_bytes() { return align16(PW_CAP * 8 + sizeof(FMid<32>)); }
@@ -1170,6 +1281,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   co.lab_isU = isU;
   co.want_side = side;
   co.wedges = (uint64_t *)dwedge;
+  co.scratch = prm.count_scratch;
   count_butterflies(a, G, co);
   uint32_t *x2lab = a.alloc<uint32_t>(nx);
   k_x2lab<<<grid_for(nx, T, cap), T, 0, a.st>>>(G.g2lab, side == 0 ? 0 : G.nu, nx, x2lab);
@@ -1266,6 +1378,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     CK(cudaFuncSetAttribute(k_peel_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)peel_block_smem()));
     CK(cudaFuncSetAttribute(k_peel_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)peel_group_smem()));
     CK(cudaFuncSetAttribute(k_fd_tip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fd_smem()));
+    CK(cudaFuncSetAttribute(k_fd_tip_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fd_smem()));
     attr = true;
   }
 
@@ -1543,6 +1656,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
         rc.want_side = side;
         rc.lab_alive = lab_alive;
         rc.wedges = (uint64_t *)(dwedge + 3);
+        rc.scratch = prm.count_scratch;
         count_butterflies(a, G, rc);
         k_gather_counts<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, state, x2lab, cnt_lab, sup);
         CK_LAUNCH();
@@ -1659,33 +1773,74 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   F.buf_big = front2;
   F.gcnt = a.zeros<uint32_t>(nx);
   F.queue = dc + 8;
-  CK(cudaMemsetAsync(dc + 8, 0, 4, a.st));
   F.wedges = dwedge + 6;
   F.steps = dwedge + 7;
   F.updates = dwedge + 9;
-  ull *pstat = a.zeros<ull>(2 * (size_t)nparts);
+  ull *pstat = a.zeros<ull>((size_t)TFD_PSTAT * nparts);
   F.pstat = pstat;
   uint32_t *seg_lo = a.alloc<uint32_t>(G.m), *seg_len = a.alloc<uint32_t>(G.m), *w_fd = a.alloc<uint32_t>(nx);
-  k_fd_segs<<<grid_for((size_t)nx * 32, T, cap), T, 0, a.st>>>(F, nx, part, seg_lo, seg_len, w_fd);
+  uint32_t *seg_n = a.alloc<uint32_t>(nx);
+  k_fd_segs<<<grid_for((size_t)nx * 32, T, cap), T, 0, a.st>>>(F, nx, part, seg_lo, seg_len, w_fd, seg_n);
   CK_LAUNCH();
   F.seg_lo = seg_lo;
   F.seg_len = seg_len;
   F.w_fd = w_fd;
-  unsigned fgrid = std::min<unsigned>(nparts, sms);
+  F.seg_n = seg_n;
+  // heavy partitions (many vertices, or far more work than the mean) on
+  // clusters of blocks on a side stream; the rest one block each, concurrently
+  const FDClusterShape fc = fd_cluster_shape((const void *)k_fd_tip_cluster, FT, fd_smem());
+  std::vector<uint32_t> heavy, light;
+  {
+    std::vector<uint32_t> hps(nparts + 1);
+    CK(cudaMemcpy(hps.data(), ps, hps.size() * 4, cudaMemcpyDeviceToHost));
+    double mean = 0;
+    for (uint32_t i = 0; i < nparts; i++) mean += (double)hwork[i];
+    mean /= std::max<uint32_t>(nparts, 1);
+    for (uint32_t i : ord)
+      (fc.size > 1 && (hps[i + 1] - hps[i] >= prm.fd_cluster_min || (double)hwork[i] > 4.0 * mean) ? heavy : light)
+          .push_back(i);
+    std::vector<uint32_t> both(heavy);
+    both.insert(both.end(), light.begin(), light.end());
+    CK(cudaMemcpyAsync(dord, both.data(), nparts * 4, cudaMemcpyHostToDevice, a.st));
+  }
+  CK(cudaMemsetAsync(dc + 8, 0, 8, a.st));  // queues of the light and heavy partitions
   g_prof.begin(PROF_FD);
-  k_fd_tip<<<fgrid, FT, fd_smem(), a.st>>>(F, fd_warp_bytes(), fd_dense_off());
-  CK_LAUNCH();
+  {
+    const uint32_t nh = (uint32_t)heavy.size(), nl = (uint32_t)light.size();
+    const uint32_t ncl = std::min<uint32_t>(nh, fc.max_clusters);
+    SideLaunch side(a.st, ncl > 0);
+    if (ncl) {
+      FDArgs FH = F;
+      FH.order = dord;
+      FH.nparts = nh;
+      FH.queue = dc + 9;
+      CK(launch_cluster((const void *)k_fd_tip_cluster, ncl, fc.size, FT, fd_smem(), side.st, FH, fd_warp_bytes(),
+                        fd_dense_off(), 4 * WIN_CAP_BIG));
+      CK_LAUNCH();
+    }
+    if (nl) {
+      FDArgs FL = F;
+      FL.order = dord + nh;
+      FL.nparts = nl;
+      unsigned fgrid = std::max<unsigned>(1u, std::min<unsigned>(nl, sms - ncl * fc.size));
+      k_fd_tip<<<fgrid, FT, fd_smem(), a.st>>>(FL, fd_warp_bytes(), fd_dense_off(), 4 * WIN_CAP);
+      CK_LAUNCH();
+    }
+  }
   g_prof.end();
   CK(cudaEventRecord(ev[4], a.st));
   CK(cudaStreamSynchronize(a.st));
   if (trace) {  // fine-phase line per partition: side partition |X_p| work steps cycles
-    std::vector<ull> pst(2 * (size_t)nparts);
+    std::vector<ull> pst((size_t)TFD_PSTAT * nparts);
     std::vector<uint32_t> hps(nparts + 1);
     CK(cudaMemcpy(pst.data(), pstat, pst.size() * 8, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(hps.data(), ps, hps.size() * 4, cudaMemcpyDeviceToHost));
-    for (uint32_t i = 0; i < nparts; i++)
-      fprintf(trace, "F %d %u %u %llu %llu %llu\n", side, i, hps[i + 1] - hps[i], (unsigned long long)hwork[i],
-              (unsigned long long)pst[2 * i], (unsigned long long)pst[2 * i + 1]);
+    // side partition |X_p| work steps cycles | cycles of select, warp path, team path | rescans heavy-vertices
+    for (uint32_t i = 0; i < nparts; i++) {
+      const ull *q = &pst[(size_t)TFD_PSTAT * i];
+      fprintf(trace, "F %d %u %u %llu %llu %llu %llu %llu %llu %llu %llu\n", side, i, hps[i + 1] - hps[i],
+              (unsigned long long)hwork[i], q[0], q[1], q[2], q[3], q[4], q[5], q[6]);
+    }
   }
   if (st) {
     ull hd[10];
@@ -1716,11 +1871,11 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       st->fd_work_sum += hwork[i];
       if (hwork[i] > st->fd_work_max) st->fd_work_max = hwork[i];
     }
-    std::vector<ull> ps_h(2 * (size_t)nparts);
+    std::vector<ull> ps_h((size_t)TFD_PSTAT * nparts);
     CK(cudaMemcpy(ps_h.data(), pstat, ps_h.size() * 8, cudaMemcpyDeviceToHost));
     for (uint32_t i = 0; i < nparts; i++) {
-      st->fd_part_steps_max = std::max<uint64_t>(st->fd_part_steps_max, ps_h[2 * i]);
-      st->fd_part_cycles_max = std::max<uint64_t>(st->fd_part_cycles_max, ps_h[2 * i + 1]);
+      st->fd_part_steps_max = std::max<uint64_t>(st->fd_part_steps_max, ps_h[(size_t)TFD_PSTAT * i]);
+      st->fd_part_cycles_max = std::max<uint64_t>(st->fd_part_cycles_max, ps_h[(size_t)TFD_PSTAT * i + 1]);
     }
   }
   for (auto &e : ev) cudaEventDestroy(e);

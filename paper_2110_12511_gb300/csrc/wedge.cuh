@@ -155,6 +155,56 @@ struct BlockGrp {
   }
 };
 
+// NT threads of a block (warps base/32 ..) synchronised by named barrier
+// `bar` (1..15; barrier 0 is __syncthreads)
+template <int NT>
+struct SubGrp {
+  static constexpr int N = NT;
+  int base, bar;
+  uint32_t *ws;              // NT/32 + 2 words of shared scratch
+  unsigned long long *ws64;  // NT/32 words (sum64 only)
+  __device__ __forceinline__ int rank() const { return (int)threadIdx.x - base; }
+  __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(NT) : "memory"); }
+  __device__ __forceinline__ uint32_t scan(uint32_t x, uint32_t *pre) const {
+    int r = rank(), l = r & 31, w = r >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (l >= o) inc += y;
+    }
+    if (l == 31) ws[w] = inc;
+    sync();
+    if (w == 0) {
+      uint32_t s = l < NT / 32 ? ws[l] : 0u, si = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, si, o);
+        if (l >= o) si += y;
+      }
+      if (l < NT / 32) ws[l] = si - s;
+      if (l == NT / 32 - 1) ws[NT / 32] = si;
+    }
+    sync();
+    pre[r] = inc - x + ws[w];
+    if (r == 0) pre[NT] = ws[NT / 32];
+    sync();
+    return pre[NT];
+  }
+  __device__ __forceinline__ uint64_t sum64(uint64_t x) const {
+    int r = rank(), l = r & 31, w = r >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (l == 0) ws64[w] = x;
+    sync();
+    uint64_t t = 0;
+    if (r == 0)
+      for (int i = 0; i < NT / 32; i++) t += ws64[i];
+    sync();
+    return t;  // valid in rank 0 only
+  }
+};
+
 // --------------------------------------------------------------- tables
 // Open-addressing hash of uint32 keys with uint32 counts in shared memory.
 struct SmemHash {

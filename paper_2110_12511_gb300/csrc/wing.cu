@@ -554,6 +554,8 @@ __device__ void wing_fd_run(const WFDArgs &A, const Team &T, uint32_t cap, uint3
     for (uint32_t j = T.tid(); j < np; j += nthr) L.a[0][j] = A.es[base + j];
     if (T.leader()) {
       S->na = np;
+      S->wn = 0;
+      S->ws = 0;
       S->nc = 0;
       S->pa = 0;
       S->pc = 0;
@@ -698,53 +700,13 @@ __global__ void __launch_bounds__(WFT) k_wing_fd_cluster(WFDArgs A, uint32_t cap
   wing_fd_run(A, T, cap, s_itm, s_lo, s_pre, bg);
 }
 
-// candidate window of a cluster team, in units of WIN_CAP per block
-#ifndef FD_CLUSTER_CAP_MULT
-#define FD_CLUSTER_CAP_MULT 2
-#endif
-
-// Cluster size for heavy partitions (16 blocks where the device can hold
-// such clusters, else 8, else 1 = no clusters) and how many clusters run at
-// once (at most half of the SMs, so that light partitions keep the rest).
-struct FDCluster {
-  uint32_t size = 1, max_clusters = 0;
-};
-FDCluster fd_cluster_shape() {
-  static FDCluster fc;
-  static bool done = false;
-  if (done) return fc;
-  done = true;
-  if (cudaFuncSetAttribute(k_wing_fd_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-    cudaGetLastError();
-  for (uint32_t cs : {16u, 8u}) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs);
-    cfg.blockDim = dim3(WFT);
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cs;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_wing_fd_cluster, &cfg) == cudaSuccess && n > 0) {
-      fc.size = cs;
-      fc.max_clusters = std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)n, (uint32_t)num_sms() / (2 * cs)));
-      return fc;
-    }
-    cudaGetLastError();
-  }
-  return fc;
-}
-
 }  // namespace
 
 // BE-Index of G (Sec. 2.3, "Construction of BE-Index"): per-edge butterfly
 // counts into sup (zeroed by the caller; Alg. 1) and counters into cctr[0..2],
 // then the blooms (k0, first pair boff), their twin pairs (pe1, pe2, pbloom)
 // and the edge -> pair lists (eoff, elink).
-void be_index_build(Arena &a, const Graph &G, unsigned long long *sup, uint64_t *cctr, BEIndex &I) {
+void be_index_build(Arena &a, const Graph &G, unsigned long long *sup, uint64_t *cctr, BEIndex &I, int scratch) {
   const int T = 256;
   const int sms = num_sms();
   const unsigned cap = 16 * sms;
@@ -757,6 +719,7 @@ void be_index_build(Arena &a, const Graph &G, unsigned long long *sup, uint64_t 
   co.wedges = cctr;
   co.be_nb = (uint64_t *)be_nb;
   co.be_np = (uint64_t *)be_np;
+  co.scratch = scratch;
   count_butterflies(a, G, co);
   a.free(cnt_lab);
   ull *bb = a.alloc<ull>((size_t)n + 1), *pb = a.alloc<ull>((size_t)n + 1);
@@ -881,7 +844,7 @@ void be_index_sums(Arena &a, const Graph &G, uint64_t *out_e, uint64_t *total, p
   ull *sup = a.zeros<ull>(m);
   uint64_t *cctr = a.zeros<uint64_t>(4);
   BEIndex I;
-  be_index_build(a, G, sup, cctr, I);
+  be_index_build(a, G, sup, cctr, I, PBNG_SCRATCH_AUTO);
   CK(cudaMemsetAsync(out_e, 0, (size_t)m * 8, a.st));
   ull *tot = a.zeros<ull>(1);
   if (I.np) {
@@ -915,7 +878,7 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   ull *sup = a.zeros<ull>(m), *init = a.alloc<ull>(m);
   uint64_t *cctr = a.zeros<uint64_t>(4);
   BEIndex I;
-  be_index_build(a, G, sup, cctr, I);
+  be_index_build(a, G, sup, cctr, I, prm.count_scratch);
   const uint32_t nb = I.nb;
   const size_t np = I.np;
   uint32_t *k0 = I.k0, *boff = I.boff, *pe1 = I.pe1, *pe2 = I.pe2, *pbloom = I.pbloom, *eoff = I.eoff,
@@ -1106,7 +1069,7 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   std::vector<uint32_t> ord(nparts);
   for (uint32_t i = 0; i < nparts; i++) ord[i] = i;
   std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return hwork[x] > hwork[y]; });
-  const FDCluster fc = fd_cluster_shape();
+  const FDClusterShape fc = fd_cluster_shape((const void *)k_wing_fd_cluster, WFT, 0);
   std::vector<uint32_t> heavy, light;
   for (uint32_t i : ord) (fc.size > 1 && hps[i + 1] - hps[i] >= prm.fd_cluster_min ? heavy : light).push_back(i);
   std::vector<uint32_t> both(heavy);
@@ -1178,46 +1141,22 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
     // one block each on the call's stream, concurrently
     const uint32_t nh = (uint32_t)heavy.size(), nl = (uint32_t)light.size();
     const uint32_t ncl = std::min<uint32_t>(nh, fc.max_clusters);
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    SideLaunch side(a.st, ncl > 0);
     if (ncl) {
-      CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
-      CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-      CK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-      CK(cudaEventRecord(fork, a.st));
-      CK(cudaStreamWaitEvent(side, fork, 0));
       WFDArgs WH = W;
       WH.orderp = dord;
       WH.nparts = nh;
       WH.queue = dc + 9;
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(ncl * fc.size);
-      cfg.blockDim = dim3(WFT);
-      cfg.stream = side;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = fc.size;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      CK(cudaLaunchKernelEx(&cfg, k_wing_fd_cluster, WH, WIN_CAP * fc.size * FD_CLUSTER_CAP_MULT));
+      CK(launch_cluster((const void *)k_wing_fd_cluster, ncl, fc.size, WFT, 0, side.st, WH, WIN_CAP_BIG));
       CK_LAUNCH();
-      CK(cudaEventRecord(join, side));
     }
     if (nl) {
       WFDArgs WL = W;
       WL.orderp = dord + nh;
       WL.nparts = nl;
       unsigned blocks = std::max<unsigned>(1u, std::min<unsigned>(nl, 2 * sms - ncl * fc.size));
-      k_wing_fd<<<blocks, WFT, 0, a.st>>>(WL, WIN_CAP);
+      k_wing_fd<<<blocks, WFT, 0, a.st>>>(WL, 4 * WIN_CAP);
       CK_LAUNCH();
-    }
-    if (ncl) {
-      CK(cudaStreamWaitEvent(a.st, join, 0));
-      cudaEventDestroy(fork);
-      cudaEventDestroy(join);
-      cudaStreamDestroy(side);
     }
   }
   g_prof.end();

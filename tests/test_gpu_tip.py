@@ -355,3 +355,56 @@ def test_propose_bounds_reproduce_the_ranges(pbng, side, P):
     th2, st2 = pbng.tip_decompose(dg, side, P=P, bounds=inner, with_stats=True)
     assert np.array_equal(pbng.as_u64(th2), oracle_tip(name, side))
     assert st2["parts_used"] == st["parts_used"]
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("cmin", [1, 0xFFFFFFFF])
+def test_tip_cluster_fine_phase(pbng, name, cmin):
+    """Fine phase with every partition peeled by a thread-block cluster
+    (cmin = 1: selection across blocks, warps of all blocks on light
+    vertices, heavy vertices counted in counters spread over the blocks'
+    shared memory) or by single blocks only: the oracle's numbers."""
+    dg = pbng.to_device(GRAPHS[name])
+    for side in ("U", "V"):
+        for P in (1, 8):
+            got = pbng.tip_decompose(dg, side, P=P, schedule={"fd_cluster_min": cmin})
+            assert np.array_equal(pbng.as_u64(got), oracle_tip(name, side))
+
+
+def test_tip_cluster_fine_phase_global_counters(pbng):
+    """A 270k-vertex partition (more than a cluster's shared counters hold):
+    the heavy vertices count in global memory; numbers equal the oracle's."""
+    g = gen.uniform(270000, 2000, 700000, 41)
+    dg = pbng.to_device(g)
+    got, st = pbng.tip_decompose(dg, "U", P=1, schedule={"fd_cluster_min": 1}, with_stats=True)
+    assert st["parts_used"] == 1
+    assert np.array_equal(pbng.as_u64(got), oracle.tip(g, "U"))
+
+
+@pytest.mark.parametrize("scratch", [0, 1, 2, 3])
+@pytest.mark.parametrize("name", ["chunglu_20k_4k_200k", "chunglu_5k_1k_50k_planted", "rand_dense_60_50", "bucket"])
+def test_counts_every_scratch_kind(pbng, name, scratch):
+    """Alg. 1 with every scratch-counter kind of the heavier starts (automatic,
+    shared hashes first, dense only, dense with 32-bit label chunks): counts
+    equal the oracle's; the 80k x 4k graph has more than 2^15 labels, so its
+    dense chunks start at label 0 and 32768 (16384 steps with 32-bit)."""
+    g = bucket_graph()[0] if name == "bucket" else GRAPHS[name]
+    dg = pbng.to_device(g)
+    cu, cv, ce = pbng.count(dg, vertices=True, edges=True, scratch=scratch)
+    assert np.array_equal(pbng.as_u64(cu), oracle.vertex_counts(g, "U"))
+    assert np.array_equal(pbng.as_u64(cv), oracle.vertex_counts(g, "V"))
+    assert np.array_equal(pbng.as_u64(ce), oracle.edge_counts(g))
+
+
+@pytest.mark.parametrize("scratch", [1, 2, 3])
+def test_tip_every_scratch_kind(pbng, scratch):
+    """The initial counts and the re-counts of a decomposition with each
+    scratch kind (re-count forced as in test_tip_recount_branch_runs)."""
+    name = "chunglu_20k_4k_200k"
+    dg = pbng.to_device(GRAPHS[name])
+    for side in ("U", "V"):
+        b0, _ = recount_bound(GRAPHS[name], side)
+        got, st = pbng.tip_decompose(dg, side, P=5, bounds=np.array([b0, 2 * b0], dtype=np.uint64),
+                                     schedule={"count_scratch": scratch}, with_stats=True)
+        assert st["recounts"] > 0
+        assert np.array_equal(pbng.as_u64(got), oracle_tip(name, side))

@@ -134,3 +134,13 @@ def test_wing_batch_matches_oracle(pbng):
     for g, n, w in zip(gs, names + [None] * 7, got):
         want = oracle_wing(n) if n is not None else oracle.wing(g)
         assert np.array_equal(pbng.as_u64(w), want)
+
+
+@pytest.mark.parametrize("scratch", [1, 2, 3])
+def test_wing_every_scratch_kind(pbng, scratch):
+    """The per-edge counts and BE-Index sizes behind the wing numbers with
+    each scratch-counter kind."""
+    name = "chunglu_5k_1k_50k_planted"
+    dg = pbng.to_device(GRAPHS[name])
+    got = pbng.wing_decompose(dg, P=20, schedule={"count_scratch": scratch})
+    assert np.array_equal(pbng.as_u64(got), oracle_wing(name))
