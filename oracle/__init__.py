@@ -25,7 +25,7 @@ def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so with gcc."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -39,6 +39,8 @@ def _get():
             f = getattr(lib, name)
             f.restype = ctypes.c_int
             f.argtypes = [U32, U32, P, P, P]
+        lib.oracle_vertex_counts_parallel.restype = ctypes.c_int
+        lib.oracle_vertex_counts_parallel.argtypes = [U32, U32, P, P, P]
         lib.oracle_vertex_support_within.restype = U64
         lib.oracle_vertex_support_within.argtypes = [U32, U32, P, P, P, P, P, U32]
         lib.oracle_edge_support_within.restype = U64
@@ -74,6 +76,17 @@ def vertex_counts(g, side="U") -> np.ndarray:
     if _get().oracle_vertex_counts(h.nu, h.nv, _p(off), _p(adj), _p(out)):
         raise MemoryError
     return out[:h.nu]
+
+
+def vertex_counts_parallel(g, side="U"):
+    """(counts, threads): the counts of vertex_counts computed by every host thread."""
+    h = _side(g, side)
+    off, adj = _csr(h)
+    out = np.zeros(max(h.nu, 1), dtype=np.uint64)
+    th = _get().oracle_vertex_counts_parallel(h.nu, h.nv, _p(off), _p(adj), _p(out))
+    if th < 0:
+        raise MemoryError
+    return out[:h.nu], th
 
 
 def edge_counts(g) -> np.ndarray:

@@ -31,6 +31,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 static uint64_t choose2(uint64_t c) { return c * (c - 1) / 2; }
 
@@ -93,6 +96,42 @@ int oracle_vertex_counts(uint32_t nu, uint32_t nv, const uint64_t *u_off, const 
   }
   free(cnt); free(list); free_vcsr(&t);
   return 0;
+}
+
+/* The same per-vertex counts computed by all host threads (OpenMP over the
+ * vertices u; each thread has its own counter array).  Used to time the
+ * counting step on every host core; returns the threads used, or -1. */
+int oracle_vertex_counts_parallel(uint32_t nu, uint32_t nv, const uint64_t *u_off, const uint32_t *u_adj, uint64_t *out) {
+  vcsr_t t;
+  if (make_vcsr(nu, nv, u_off, u_adj, &t)) return -1;
+  int threads = 1, failed = 0;
+#ifdef _OPENMP
+#pragma omp parallel reduction(| : failed)
+#endif
+  {
+#ifdef _OPENMP
+#pragma omp single
+    threads = omp_get_num_threads();
+#endif
+    uint32_t *cnt = (uint32_t *)calloc((size_t)nu + 1, sizeof(uint32_t));
+    uint32_t *list = (uint32_t *)malloc(((size_t)nu + 1) * sizeof(uint32_t));
+    if (!cnt || !list) {
+      failed = 1;
+    } else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+      for (int64_t ui = 0; ui < (int64_t)nu; ui++) {
+        uint32_t u = (uint32_t)ui;
+        uint64_t nt = common_counts(u, u_off, u_adj, &t, NULL, cnt, list), s = 0;
+        for (uint64_t i = 0; i < nt; i++) { s += choose2(cnt[list[i]]); cnt[list[i]] = 0; }
+        out[u] = s;
+      }
+    }
+    free(cnt); free(list);
+  }
+  free_vcsr(&t);
+  return failed ? -1 : threads;
 }
 
 /* Per-edge butterfly counts: out[(u,v)] = sum_{u' in N_v, u' != u} (c(u,u') - 1). */

@@ -165,3 +165,13 @@ def test_support_within_matches_definition():
     for e in range(g.m):
         want = sum(1 for bf in bfs if e in bf and all(emember[x] for x in bf if x != e))
         assert t.edge_support_within(emember, e) == want
+
+
+def test_parallel_vertex_counts_equal_sequential():
+    """The all-cores counting used for the CPU baseline computes the same
+    definition as vertex_counts (Sec. 2.1), on both sides."""
+    for g in (gen.make("chunglu_5k_1k_50k_planted"), gen.complete(7, 5), gen.from_edges(3, 2, [], [])):
+        for side in ("U", "V"):
+            got, threads = oracle.vertex_counts_parallel(g, side)
+            assert threads >= 1
+            assert np.array_equal(got, oracle.vertex_counts(g, side))
