@@ -106,6 +106,12 @@ typedef struct pbng_opts {
                                16-bit, over chunks of 32768 labels beyond the first 16384),
                                PBNG_SCRATCH_DENSE32 (the same with 32-bit counters); results are
                                identical */
+  float learned_vet;        /* LEARNED: the estimator judges each learned bound by the work of the
+                               range it closes; a range holding more than learned_vet times the
+                               estimator's target work (remaining work over remaining partitions)
+                               takes the estimator's bound instead.  0 = default (2.0); negative =
+                               learned bounds are not judged; NaN is rejected.  Results are
+                               identical */
 } pbng_opts;
 
 enum { PBNG_SCRATCH_AUTO = 0, PBNG_SCRATCH_HASH = 1, PBNG_SCRATCH_DENSE = 2, PBNG_SCRATCH_DENSE32 = 3 };

@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
                 ("bounds_out", ctypes.c_void_p), ("n_bounds_out", ctypes.c_uint32),
                 ("bucket_shift", ctypes.c_uint32), ("warp_max_w", ctypes.c_uint32),
                 ("group_max_w", ctypes.c_uint32), ("item_w", ctypes.c_uint32), ("fd_cluster_min", ctypes.c_uint32),
-                ("count_scratch", ctypes.c_uint32)]
+                ("count_scratch", ctypes.c_uint32), ("learned_vet", ctypes.c_float)]
 
 
 class Stats(ctypes.Structure):
@@ -162,7 +162,7 @@ SCRATCH_AUTO, SCRATCH_HASH, SCRATCH_DENSE, SCRATCH_DENSE32 = 0, 1, 2, 3
 
 
 def _opts(stream=None, bounds=None, recount=True, compact=True, mem=MEM_DEVICE, graph_rounds=False, keep=None,
-          mlp=None, bounds_out=None, bucket_shift=0, schedule=None):
+          mlp=None, bounds_out=None, bucket_shift=0, schedule=None, learned_vet=0.0):
     o = Opts()
     lib().pbng_opts_init(ctypes.byref(o))
     o.bucket_shift = int(bucket_shift)
@@ -191,6 +191,7 @@ def _opts(stream=None, bounds=None, recount=True, compact=True, mem=MEM_DEVICE, 
         o.n_bounds = b.size
     if mlp is not None:  # (params tensor on the device, hidden, out)
         o.bounds_mode = BOUNDS_LEARNED
+        o.learned_vet = float(learned_vet)
         o.mlp_params = ctypes.c_void_p(mlp[0].data_ptr())
         o.mlp_hidden, o.mlp_out = int(mlp[1]), int(mlp[2])
     if bounds_out is not None:
@@ -228,18 +229,21 @@ def _side(side) -> int:
 
 
 def tip_decompose(dg: DeviceGraph, side="U", P=150, bounds=None, recount=True, compact=True, graph_rounds=False,
-                  stream=None, with_stats=False, mlp=None, bounds_out=None, bucket_shift=0, schedule=None):
+                  stream=None, with_stats=False, mlp=None, bounds_out=None, bucket_shift=0, schedule=None,
+                  learned_vet=0.0):
     """Tip numbers of one side (two-phase PBNG, Sec. 3.1-3.2).
 
     bounds: explicit upper bounds; mlp: (params, hidden, out) of the learned
-    proposer; bounds_out: numpy uint64 array receiving the bounds used."""
+    proposer, whose bounds the estimator judges (learned_vet: most work of a
+    learned range as a multiple of the estimator's target, 0 = 2.0, negative
+    = unjudged); bounds_out: numpy uint64 array receiving the bounds used."""
     import torch
     s = _side(side)
     n = dg.nu if s == SIDE_U else dg.nv
     out = torch.empty(max(n, 1), dtype=torch.int64, device=dg.u_off.device)
     keep = []
     o = _opts(stream, bounds, recount, compact, graph_rounds=graph_rounds, keep=keep, mlp=mlp, bounds_out=bounds_out,
-              bucket_shift=bucket_shift, schedule=schedule)
+              bucket_shift=bucket_shift, schedule=schedule, learned_vet=learned_vet)
     st = Stats()
     g = dg.c_struct()
     rc = lib().pbng_tip_decompose(ctypes.byref(g), s, int(P), out.data_ptr(), ctypes.byref(o), ctypes.byref(st))
@@ -254,7 +258,8 @@ def propose_bounds(dg: DeviceGraph, side="U", P=150, mlp=None, bounds=None, stre
     out = np.zeros(int(P) + 1, dtype=np.uint64)
     keep = []
     o = _opts(stream, bounds, kw.get("recount", True), kw.get("compact", True), keep=keep, mlp=mlp,
-              graph_rounds=kw.get("graph_rounds", False), schedule=kw.get("schedule"))
+              graph_rounds=kw.get("graph_rounds", False), schedule=kw.get("schedule"),
+              learned_vet=kw.get("learned_vet", 0.0))
     g = dg.c_struct()
     _check(lib().pbng_propose_bounds(ctypes.byref(g), _side(side), int(P), out.ctypes.data, ctypes.byref(o)),
            "pbng_propose_bounds")

@@ -114,6 +114,8 @@ TipParams tip_params(uint32_t P, const pbng_opts &o) {
   p.fd_cluster_min = o.fd_cluster_min ? o.fd_cluster_min : 32768u;
   if (o.count_scratch > PBNG_SCRATCH_DENSE32) fail(PBNG_EINVAL, "unknown count_scratch %u", o.count_scratch);
   p.count_scratch = (int)o.count_scratch;
+  if (o.learned_vet != o.learned_vet) fail(PBNG_EINVAL, "learned_vet is NaN");
+  p.learned_vet = o.learned_vet == 0.0f ? 2.0 : (o.learned_vet < 0.0f ? 0.0 : (double)o.learned_vet);
   p.timeout_ns = o.timeout_ns ? o.timeout_ns : 10000000000ull;
   p.mlp_params = o.mlp_params;
   p.mlp_hidden = o.mlp_hidden;

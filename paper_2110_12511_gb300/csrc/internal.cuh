@@ -204,6 +204,7 @@ struct TipParams {
   uint32_t warp_max_w, group_max_w, item_w;  // coarse-peel schedule, 0 = default
   uint32_t fd_cluster_min;                   // fine phase: smallest partition for a cluster team
   int count_scratch;                         // counting: scratch counters (PBNG_SCRATCH_*)
+  double learned_vet;                        // learned bounds: most work of a range, x target (<= 0: unjudged)
   uint64_t timeout_ns;
   const float *mlp_params;  // learned bounds (bounds_mode == PBNG_BOUNDS_LEARNED)
   uint32_t mlp_hidden, mlp_out;

@@ -46,7 +46,6 @@ constexpr uint32_t P_CHUNK = 2 * PB_CAP;         // block-class dense counters (
 constexpr uint32_t BK_SHIFT_MIN = 14;            // target buckets are at least P_CHUNK ids wide
 constexpr uint64_t BOFF_BUDGET = 2ull << 30;     // most bytes of bucket offsets
 constexpr uint64_t ITEM_W = 32768;               // wedges per block-class work item (at least)
-constexpr double LEARNED_VET = 2.0;              // a learned range may hold 2x the estimator's target work
 constexpr int PB_PER_SM = 3;                     // resident blocks per SM (shared memory bound)
 constexpr uint32_t P_DENSE = 16384;              // fine phase: dense shared counters when |X_p| <= this
 constexpr int PBT = 512, PWT = 256;
@@ -1527,7 +1526,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     set_u64(a, (uint64_t *)&rs->kmin, ~0ull);
     // the work proxy is only needed when find_range will run, or when the
     // estimator vets a learned bound
-    const bool vetted = prm.bounds_mode == PBNG_BOUNDS_LEARNED && !last;
+    const bool vetted = prm.bounds_mode == PBNG_BOUNDS_LEARNED && !last && prm.learned_vet > 0;
     bool given = last || (explicit_bounds && pi < n_bounds);
     ull hk[3];
     if (given && !vetted) {
@@ -1565,7 +1564,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     uint64_t init_est = 0;
     if (!use_est && vetted && wsum > 0) {
       // the plain estimator vets a learned bound: its range may hold at
-      // most LEARNED_VET times the estimator's target work, else the
+      // most learned_vet times the estimator's target work, else the
       // estimator's own bound is used
       double t = (double)wsum * scale / (double)(P - pi);
       ull *d = a.zeros<ull>(1), wb = 0;
@@ -1574,7 +1573,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
       CK(cudaMemcpyAsync(&wb, d, 8, cudaMemcpyDeviceToHost, a.st));
       CK(cudaStreamSynchronize(a.st));
       a.free(d);
-      if ((double)wb > LEARNED_VET * std::max(t, 1.0)) use_est = true;
+      if ((double)wb > prm.learned_vet * std::max(t, 1.0)) use_est = true;
       else init_est = wb;
     }
     if (use_est) {

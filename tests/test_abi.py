@@ -41,14 +41,14 @@ def test_every_declared_symbol_is_exported(L):
 def test_struct_layout_matches_header(tmp_path):
     import paper_2110_12511_gb300 as pbng
     src = tmp_path / "sz.c"
-    src.write_text('#include "pbng.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(){printf("%zu %zu %zu %zu %zu\\n",'
+    src.write_text('#include "pbng.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(){printf("%zu %zu %zu %zu %zu %zu\\n",'
                    'sizeof(pbng_bigraph),sizeof(pbng_opts),sizeof(pbng_stats),offsetof(pbng_opts,stream),'
-                   'offsetof(pbng_stats,parts_used));return 0;}\n')
+                   'offsetof(pbng_stats,parts_used),offsetof(pbng_opts,learned_vet));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(pbng.Bigraph), ctypes.sizeof(pbng.Opts), ctypes.sizeof(pbng.Stats),
-            pbng.Opts.stream.offset, pbng.Stats.parts_used.offset]
+            pbng.Opts.stream.offset, pbng.Stats.parts_used.offset, pbng.Opts.learned_vet.offset]
     assert got == want
 
 
@@ -73,6 +73,12 @@ def test_host_side_argument_checks(L):
     o.n_bounds = 3
     assert L.pbng_tip_decompose(ctypes.byref(g), 0, 4, out.ctypes.data, ctypes.byref(o), None) == pbng.PBNG_EBOUNDS
     assert b"increasing" in L.pbng_last_error_detail()
+    # a NaN learned-bound judge
+    o.bounds_mode = 0
+    o.learned_vet = float("nan")
+    assert L.pbng_tip_decompose(ctypes.byref(g), 0, 4, out.ctypes.data, ctypes.byref(o), None) == pbng.PBNG_EINVAL
+    assert b"learned_vet" in L.pbng_last_error_detail()
+    o.learned_vet = 0.0
     # oversize graph
     big = pbng.Bigraph(1 << 30, 1 << 30, 0, off.ctypes.data, 0)
     o.bounds_mode = 0

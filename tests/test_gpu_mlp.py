@@ -118,6 +118,20 @@ def test_learned_bounds_give_identical_tip_numbers(pbng, name):
     assert (np.diff(b.astype(np.float64)) > 0).all()
 
 
+@pytest.mark.parametrize("vet", [-1.0, 0.5, 4.0])
+def test_learned_judge_setting_gives_identical_tip_numbers(pbng, vet):
+    """Learned bounds unjudged (negative learned_vet), judged strictly and
+    loosely: the tip numbers are the oracle's in every case (Th. 2)."""
+    import torch
+    from paper_2110_12511_gb300 import learned
+    g = gen.make("chunglu_20k_4k_200k")
+    dg = pbng.to_device(g)
+    mlp = learned.load(WEIGHTS) if os.path.exists(WEIGHTS) else (
+        torch.as_tensor(learned.init_params(199, 1), device="cuda"), 128, 199)
+    th = pbng.tip_decompose(dg, "U", P=200, mlp=mlp, learned_vet=vet)
+    assert np.array_equal(pbng.as_u64(th), oracle.tip(g, "U"))
+
+
 def test_propose_bounds_learned(pbng):
     """pbng_propose_bounds with the learned proposer: the bounds the coarse
     phase uses (learned proposals judged by the estimator) reproduce the
