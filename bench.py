@@ -393,6 +393,47 @@ def run_extra(args):
         else:  # partition count sweep, both sides, default configuration
             for side in ("U", "V"):
                 res[side] = {str(P): run(side, P) for P in (10, 50, 150, 400, 1000)}
+    elif args.workload in ("wing_ablation", "wing_p_sweep", "wing_learned"):
+        g = gen.make(WING_WORKLOAD)
+        dg = pbng.to_device(g, dev)
+
+        def run_w(P, **kw):
+            pbng.wing_decompose(dg, P=P, **kw)  # warm
+            t, (th, st) = timed(lambda: pbng.wing_decompose(dg, P=P, with_stats=True, **kw), dev, flush)
+            return th, {"ms": t, "links": st["links"], "updates": st["updates"], "rounds": st["rounds"],
+                        "parts_used": st["parts_used"], "fd_steps_max": st["fd_part_steps_max"],
+                        "phase_ms": {k: st["ns_" + k] / 1e6 for k in ("count", "cd", "part", "fd")},
+                        "fd_work_max": st["fd_work_max"], "fd_work_sum": st["fd_work_sum"]}
+
+        res["m"] = g.m
+        if args.workload == "wing_ablation":
+            # Sec. 6 ablations for wing: PBNG, PBNG- (no dynamic BE-Index updates:
+            # pair lists are never compacted)
+            ref = None
+            for name, kw in {"PBNG": {}, "PBNG-": {"compact": False}}.items():
+                th, res[name] = run_w(WING_P, **kw)
+                th = pbng.as_u64(th)
+                ref = th if ref is None else ref
+                assert (th == ref).all(), "ablation changed the wing numbers"
+        elif args.workload == "wing_p_sweep":
+            for P in (25, 50, 100, 200, 400, 1000):
+                res[str(P)] = run_w(P)[1]
+        else:  # learned wing bounds against the estimator (judged by default, and unjudged)
+            from paper_2110_12511_gb300 import learned
+            mlp = learned.load(learned.WING_WEIGHTS, device=dev)
+            ref = None
+            for name, kw in {"estimator": {}, "learned": {"mlp": mlp}, "learned_unjudged":
+                             {"mlp": mlp, "learned_vet": -1.0}}.items():
+                best = None
+                for _ in range(2):
+                    th, r = run_w(WING_P, **kw)
+                    best = r if best is None or r["ms"] < best["ms"] else best
+                th = pbng.as_u64(th)
+                ref = th if ref is None else ref
+                assert (th == ref).all(), "learned bounds changed the wing numbers"
+                res[name] = best
+            res["ratio"] = res["estimator"]["ms"] / res["learned"]["ms"]
+            res["ratio_unjudged"] = res["estimator"]["ms"] / res["learned_unjudged"]["ms"]
     else:
         raise SystemExit(f"unknown workload {args.workload}")
     print(json.dumps(res), flush=True)
@@ -509,7 +550,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="default: the bench line; others: tip_uniform_2k_1k_20k, wing_chunglu_500k_100k_5m_planted, "
                          "tip_batch_4096, tip_chunglu_5m_1m_60m, tip_chunglu_5m_1m_60m_learned, tip_ablation, "
-                         "tip_p_sweep, tip_components")
+                         "tip_p_sweep, tip_components, wing_ablation, wing_p_sweep, wing_learned")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--host-rounds", dest="graph_rounds", action="store_false",
                     help="drive the coarse rounds from the host (default: one CUDA graph per range, device loop)")
@@ -678,6 +719,20 @@ def main():
                 full["gpu_ms_per_step"] = ms_step
                 full["time_ratio"] = full["seconds"] / (ms_step / 1e3)
                 cpu["full_graph"] = full
+            # the counting step alone, like for like: the oracle's per-vertex
+            # counts of the U side of the full graph on every host core against
+            # the GPU's counting phase of the U-side decomposition
+            t0 = time.perf_counter()
+            _, threads = oracle.vertex_counts_parallel(g, "U")
+            dt_c = time.perf_counter() - t0
+            dvf = np.bincount(g.u_adj, minlength=g.nv).astype(np.float64)
+            gpu_count_ms = stats[0][0]["ns_count"] / 1e6
+            cpu["count_all_cores"] = {
+                "what": "per-vertex butterfly counts of the U side of the full graph (Sec. 2.1 definition, 2-hop "
+                        "traversal), oracle on every host thread", "cores": threads, "host": platform.machine(),
+                "seconds": dt_c, "wedge_visits": float((dvf ** 2).sum()),
+                "value": float((dvf ** 2).sum()) / dt_c, "unit": "wedges/s",
+                "gpu_count_phase_ms": gpu_count_ms, "time_ratio": dt_c / (gpu_count_ms / 1e3)}
         s0u, s0v = stats[0]
         line = {
             "metric": "tip decomposition wedges/s (both sides)", "value": value, "unit": "wedges/s", "n_gpus": ws,

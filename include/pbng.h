@@ -76,8 +76,10 @@ typedef struct pbng_opts {
                               `recount` is not used; results are identical.  Default 0 */
   uint64_t timeout_ns;     /* limit for bounded device waits; 0 = 10 s */
   void *stream;            /* cudaStream_t */
-  const float *mlp_params; /* LEARNED (tip): device float32 parameters, layout of pbng_mlp_forward,
-                              in = 128 features of pbng_bound_features, out = bounds proposed */
+  const float *mlp_params; /* LEARNED: device float32 parameters, layout of pbng_mlp_forward, in =
+                              128 features (pbng_bound_features for tip, pbng_wing_bound_features
+                              for wing), out = bounds proposed; the estimator judges each bound
+                              (learned_vet below) */
   uint32_t mlp_hidden, mlp_out;
   uint64_t *bounds_out;    /* optional host array receiving the upper bounds theta(2), theta(3), ...
                               actually used (the last, unbounded range is not listed) */
@@ -279,6 +281,12 @@ int pbng_be_index_sums(const pbng_bigraph *g, uint64_t *out_e, uint64_t *out_tot
  * The proposer's outputs are relative to the largest count K:
  * y_i = log2(1 + b_i) / log2(1 + K).  out: 128 floats of device memory. */
 int pbng_bound_features(const pbng_bigraph *g, pbng_side side, float *out, const pbng_opts *opts);
+
+/* Features of the learned wing bound proposer, the same histograms over the
+ * edges: out[0..63] by the half-octave bin of min(d_u, d_v) of each edge,
+ * out[64..127] by how many bits each edge's initial butterfly count (Sec. 2.1,
+ * per edge) lies below the largest one.  out: 128 floats of device memory. */
+int pbng_wing_bound_features(const pbng_bigraph *g, float *out, const pbng_opts *opts);
 
 /* MLP of the learned proposer, FP32, on the device.  params packs
  * [W1 (in x hidden), b1, W2 (hidden x hidden), b2, W3 (hidden x out), b3]

@@ -105,6 +105,8 @@ def lib():
         L.pbng_version.restype = C
         L.pbng_bound_features.argtypes = [G, C, P, O]
         L.pbng_bound_features.restype = C
+        L.pbng_wing_bound_features.argtypes = [G, P, O]
+        L.pbng_wing_bound_features.restype = C
         L.pbng_mlp_forward.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_uint32, P, P]
         L.pbng_mlp_forward.restype = C
         L.pbng_mlp_grad.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P, P, ctypes.c_uint32, P, P, P]
@@ -291,6 +293,17 @@ def bound_features(dg: DeviceGraph, side="U", stream=None):
     return out
 
 
+def wing_bound_features(dg: DeviceGraph, stream=None):
+    """128 histogram features of the learned wing bound proposer (float32 tensor)."""
+    import torch
+    out = torch.zeros(128, dtype=torch.float32, device=dg.u_off.device)
+    o = _opts(stream)
+    g = dg.c_struct()
+    _check(lib().pbng_wing_bound_features(ctypes.byref(g), out.data_ptr(), ctypes.byref(o)),
+           "pbng_wing_bound_features")
+    return out
+
+
 def _cs(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -341,12 +354,15 @@ def tip_decompose_host(g, side="U", P=150, with_stats=False, **kw):
 
 
 def wing_decompose(dg: DeviceGraph, P=400, bounds=None, recount=True, compact=True, stream=None, with_stats=False,
-                   schedule=None, bounds_out=None):
-    """Wing numbers of every edge (BE-Index PBNG, Sec. 3.3)."""
+                   schedule=None, bounds_out=None, mlp=None, learned_vet=0.0):
+    """Wing numbers of every edge (BE-Index PBNG, Sec. 3.3); mlp: (params,
+    hidden, out) of the learned wing bound proposer, learned_vet as for
+    tip_decompose."""
     import torch
     out = torch.empty(max(dg.m, 1), dtype=torch.int64, device=dg.u_off.device)
     keep = []
-    o = _opts(stream, bounds, recount, compact, keep=keep, schedule=schedule, bounds_out=bounds_out)
+    o = _opts(stream, bounds, recount, compact, keep=keep, schedule=schedule, bounds_out=bounds_out, mlp=mlp,
+              learned_vet=learned_vet)
     st = Stats()
     g = dg.c_struct()
     rc = lib().pbng_wing_decompose(ctypes.byref(g), int(P), out.data_ptr(), ctypes.byref(o), ctypes.byref(st))

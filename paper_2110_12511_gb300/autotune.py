@@ -8,7 +8,11 @@ same supports, Sec. 3.1; any bounds give the same numbers, Th. 2):
 - ``warp_max_w`` / ``group_max_w``: wedge limits of the warp and 256-thread
   group classes of active vertices (the rest go to blocks);
 - ``item_w``: wedges per block work item (splitting of heavy vertices);
-- ``bucket_shift``: width 2^shift of the target-id buckets of block items.
+- ``bucket_shift``: width 2^shift of the target-id buckets of block items;
+- ``count_scratch``: scratch counters of the heavier counting starts
+  (automatic, shared hashes first, dense shared label chunks);
+- ``fd_cluster_min``: smallest fine-phase partition peeled by a
+  thread-block cluster instead of one block (0 = the default 32768).
 
 The tuner times candidate schedules on the caller's graph with CUDA events and
 keeps the fastest, searching one knob at a time from the defaults (coordinate
@@ -22,7 +26,8 @@ import json
 import os
 import time
 
-DEFAULT = {"graph_rounds": False, "warp_max_w": 0, "group_max_w": 0, "item_w": 0, "bucket_shift": 0}
+DEFAULT = {"graph_rounds": False, "warp_max_w": 0, "group_max_w": 0, "item_w": 0, "bucket_shift": 0,
+           "count_scratch": 0, "fd_cluster_min": 0}
 
 # candidate values per knob (0 = the library's default)
 SPACE = {
@@ -31,6 +36,8 @@ SPACE = {
     "group_max_w": [0, 1024, 512],
     "item_w": [0, 8192, 131072],
     "bucket_shift": [0, 14, 16],
+    "count_scratch": [0, 1, 2],
+    "fd_cluster_min": [0, 8192, 0xFFFFFFFF],
 }
 
 WARP_MAX, GROUP_MAX = 512, 2048  # the library's limits (include/pbng.h)
@@ -47,7 +54,9 @@ def valid(cfg):
     wm, gm = effective(cfg)
     iw = cfg.get("item_w") or 0
     sh = cfg.get("bucket_shift") or 0
-    return wm <= WARP_MAX and gm <= GROUP_MAX and wm <= gm and (iw == 0 or iw >= 4096) and (sh == 0 or 14 <= sh <= 30)
+    cs = cfg.get("count_scratch") or 0
+    return (wm <= WARP_MAX and gm <= GROUP_MAX and wm <= gm and (iw == 0 or iw >= 4096) and (sh == 0 or 14 <= sh <= 30)
+            and 0 <= cs <= 3)
 
 
 def coordinate_search(measure, space=None, start=None, rounds=1):
@@ -77,7 +86,7 @@ def coordinate_search(measure, space=None, start=None, rounds=1):
 
 def split(cfg):
     """(keyword arguments of tip_decompose) for a schedule cfg."""
-    sched = {k: int(cfg.get(k) or 0) for k in ("warp_max_w", "group_max_w", "item_w")}
+    sched = {k: int(cfg.get(k) or 0) for k in ("warp_max_w", "group_max_w", "item_w", "count_scratch", "fd_cluster_min")}
     return {"graph_rounds": bool(cfg.get("graph_rounds")), "bucket_shift": int(cfg.get("bucket_shift") or 0),
             "schedule": sched}
 

@@ -478,6 +478,28 @@ int pbng_bound_features(const pbng_bigraph *g, pbng_side side, float *out, const
   });
 }
 
+int pbng_wing_bound_features(const pbng_bigraph *g, float *out, const pbng_opts *opts) {
+  pbng_opts o = opts ? *opts : defaults();
+  return guarded([&] {
+    if (!out) fail(PBNG_EINVAL, "null output");
+    check_graph(g);
+    init_device_pool();
+    Arena a((cudaStream_t)o.stream);
+    pbng_bigraph d = device_graph(a, g, o.mem);
+    Graph G;
+    build_graph(a, d, true, true, G);
+    uint64_t *cnt = a.zeros<uint64_t>((size_t)G.n + 1), *cnt_e = a.zeros<uint64_t>((size_t)G.m + 1);
+    uint32_t *edeg = a.alloc<uint32_t>((size_t)G.m + 1);
+    CountOut co;
+    co.cnt_lab = cnt;
+    co.cnt_e = cnt_e;
+    count_butterflies(a, G, co);
+    edge_min_degrees(a, G, edeg);
+    bound_features(a, cnt_e, nullptr, G.m, out, edeg);
+    CK(cudaStreamSynchronize(a.st));
+  });
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------ batch

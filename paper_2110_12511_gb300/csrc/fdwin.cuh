@@ -46,6 +46,8 @@ struct FDShared {
   uint32_t p;        // partition being peeled
   uint32_t nt, ncq;  // per-step work lists of the kernels (touched groups, compaction queue)
   uint32_t wn, ws;   // entities of the current window when it was chosen, steps taken since
+  uint32_t ng, nh;   // per-step group queue and its overflow list (tip kernels)
+  uint32_t nbq, nbh; // per-step block queue and its overflow list (tip cluster kernels)
 };
 
 // per-block scratch of a team's minimum reduction
@@ -228,6 +230,10 @@ __device__ uint32_t fd_select(const Team &T, const FDLists &L, unsigned long lon
     S->nn = 0;
     S->nt = 0;  // the kernels' per-step lists start empty
     S->ncq = 0;
+    S->ng = 0;
+    S->nh = 0;
+    S->nbq = 0;
+    S->nbh = 0;
   }
   T.sync();
   const unsigned long long level = *(volatile unsigned long long *)&S->level;

@@ -224,7 +224,11 @@ void wing_components(Arena &a, Graph &G, const uint64_t *theta, uint64_t k, uint
                      uint64_t *joins);
 
 // ------------------------------------------------------- learned bounds
-uint64_t bound_features(Arena &a, const uint64_t *sup, const uint32_t *p_off, uint32_t nx, float *out128);
+uint64_t bound_features(Arena &a, const uint64_t *sup, const uint32_t *p_off, uint32_t nx, float *out128,
+                        const uint32_t *deg = nullptr);
+// min(d_u, d_v) of every edge (U-CSR order): the degree of an edge in the
+// wing proposer's features
+void edge_min_degrees(Arena &a, const Graph &G, uint32_t *out);
 std::vector<uint64_t> propose_bounds(Arena &a, const float *params, uint32_t hidden, uint32_t out, const float *feat,
                                      uint64_t max_support);
 

@@ -121,15 +121,16 @@ __global__ void k_max_u64(const unsigned long long *x, uint32_t n, unsigned long
   if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
 }
 
-__global__ void k_features(const unsigned long long *sup, const uint32_t *p_off, uint32_t nx, const unsigned long long *mx,
-                           float *hist) {
+// degree of entity x: from the CSR offsets (vertices) or given (edges)
+__global__ void k_features(const unsigned long long *sup, const uint32_t *p_off, const uint32_t *deg, uint32_t nx,
+                           const unsigned long long *mx, float *hist) {
   __shared__ unsigned int h[128];
   if (threadIdx.x < 128) h[threadIdx.x] = 0;
   __syncthreads();
   unsigned long long K = *mx;
   int kb = K ? 64 - __clzll(K) : 0;
   for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < nx; x += (size_t)gridDim.x * blockDim.x) {
-    uint32_t d = p_off[x + 1] - p_off[x];
+    uint32_t d = deg ? deg[x] : p_off[x + 1] - p_off[x];
     int db = d;
     if (d >= 2) {
       int L = 32 - __clz(d);
@@ -146,15 +147,17 @@ __global__ void k_features(const unsigned long long *sup, const uint32_t *p_off,
 
 }  // namespace
 
-// features of the peeled side from its initial supports (device arrays);
-// returns the largest initial support
-uint64_t bound_features(Arena &a, const uint64_t *sup, const uint32_t *p_off, uint32_t nx, float *out128) {
+// features of the peeled entities from their initial supports and degrees
+// (device arrays; deg null: degrees from p_off); returns the largest support
+uint64_t bound_features(Arena &a, const uint64_t *sup, const uint32_t *p_off, uint32_t nx, float *out128,
+                        const uint32_t *deg) {
   CK(cudaMemsetAsync(out128, 0, 128 * sizeof(float), a.st));
   if (!nx) return 0;
   unsigned long long *mx = a.zeros<unsigned long long>(1);
   k_max_u64<<<grid_for(nx, 256, 4 * num_sms()), 256, 0, a.st>>>((const unsigned long long *)sup, nx, mx);
   CK_LAUNCH();
-  k_features<<<grid_for(nx, 256, 4 * num_sms()), 256, 0, a.st>>>((const unsigned long long *)sup, p_off, nx, mx, out128);
+  k_features<<<grid_for(nx, 256, 4 * num_sms()), 256, 0, a.st>>>((const unsigned long long *)sup, p_off, deg, nx, mx,
+                                                                   out128);
   CK_LAUNCH();
   uint64_t K = fetch(a, (const uint64_t *)mx);
   a.free(mx);

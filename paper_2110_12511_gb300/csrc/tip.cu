@@ -37,7 +37,11 @@ enum : uint8_t { ST_ALIVE = 0, ST_ACTIVE = 1, ST_PEELED = 2 };
 
 constexpr uint32_t PW_MAXW = 256, PW_CAP = 512;  // fine phase: warp-per-vertex shared hash
 constexpr uint32_t FEW_VERTICES = 8, WARP_FEW_W = 192;  // fine phase: few peeled vertices -> team-wide above this
-constexpr uint32_t HW_KEEP = 4;  // fine phase, team path: wedges a thread keeps between its two passes
+constexpr uint32_t HW_KEEP = 4;
+constexpr int FGT = 128;                           // fine phase: threads of a group (four per block)
+constexpr uint32_t FG_CAP = 2048, FG_MAXW = 1024;  // group hash slots (in the dense counters' memory), most wedges
+constexpr uint32_t FG_MIN_BIG = 8;                 // heavy vertices of a step from which groups take them
+constexpr uint32_t FB_MAXW = 4096;                 // cluster teams: most wedges of a vertex one block takes  // fine phase, team path: wedges a thread keeps between its two passes
 constexpr uint32_t QW_MAXW = 512, QW_CAP = 1024;  // coarse peel: warp-per-vertex shared hash
 constexpr uint32_t QG_MAXW = 2048, QG_CAP = 4096; // coarse peel: 256-thread group per vertex
 constexpr int QGT = 256;                          // threads of a group
@@ -838,6 +842,7 @@ struct FDArgs {
   ull *sup;  // starts as init
   ull *theta;
   uint32_t *buf_a, *buf_b, *buf_c, *buf_d, *buf_f, *buf_big;  // per-partition regions (offset ps[p])
+  uint32_t *buf_huge;                                        // heavy vertices left by the groups (offset ps[p])
   uint32_t *gcnt;                             // per-partition dense counters (offset ps[p]), zeroed
   unsigned *queue;
   ull *wedges, *steps, *updates;
@@ -848,7 +853,7 @@ struct FDArgs {
 };
 
 constexpr int FT = 512, FW = FT / 32;
-constexpr int TFD_PSTAT = 7;  // per-partition statistics of the fine phase
+constexpr int TFD_PSTAT = 9;  // per-partition statistics of the fine phase
 
 template <int N>
 struct FMid {
@@ -942,16 +947,58 @@ struct FDCounters {
   }
 };
 
+// per-group scratch of the fine phase's group tier: slices and scan words
+__host__ __device__ constexpr size_t fd_group_bytes() { return align16(sizeof(FMid<FGT>)) + 32; }
+static_assert((FT / FGT) * FG_CAP * 8 <= P_DENSE * 4, "group hashes fit the dense counters' memory");
+static_assert(2 * FB_MAXW * 8 <= P_DENSE * 4, "a block hash fits the dense counters' memory");
+static_assert((FT / FGT) <= 15, "named barriers 1..groups");
+
+// Count the alive targets of x's wedges in G_p into a shared hash of 64-bit
+// slots ((id + 1) << 32 | count, zero = empty) held by group g, then drain it
+// (decrements C(c, 2), crossings into cand) leaving it zeroed; returns updates
+template <class Grp, int N>
+__device__ __forceinline__ uint64_t fd_hash_vertex(const FDArgs &A, const Grp &g, FMid<N> &mb, uint32_t p, uint32_t x,
+                                                   uint32_t W, unsigned long long *slot, unsigned *nc, uint32_t *cand,
+                                                   ull hi) {
+  const uint32_t xo = A.p_off[x], xd = A.seg_n[x];
+  const uint32_t capg = pow2_at_least(max(2u * W, 64u));
+  WHash h{slot, capg - 1};
+  for (uint32_t b0 = 0; b0 < xd; b0 += N) {
+    const uint32_t Tw = fd_load(A, p, xo, xd, b0, g, mb);
+    fd_walk(A, g, mb, Tw, [&](uint32_t xp) {
+      if (ldt(&A.state[xp]) == ST_ALIVE) h.inc(xp);
+    });
+    g.sync();
+  }
+  uint64_t nup = 0;
+  for (uint32_t i = g.rank(); i < capg; i += N) {
+    const unsigned long long v = slot[i];
+    if (!v) continue;
+    slot[i] = 0;
+    const uint32_t c = (uint32_t)v;
+    if (c >= 2) {
+      const uint32_t xp = (uint32_t)(v >> 32) - 1;
+      const ull dec = choose2(c);
+      fd_crossing(nc, cand, hi, xp, atomicAdd(&A.sup[xp], (ull)(0ull - dec)), dec);
+      nup++;
+    }
+  }
+  g.sync();
+  return nup;
+}
+
 // Fine phase of the partitions handed out by A.queue / A.order (Sec. 3.1.2,
 // 3.2): bottom-up peeling of G_p from init, one partition at a time per team.
 // Each step: the selection (fd_select), then the updates of the peeled
-// vertices - a warp per vertex with few wedges in G_p (shared hash), the
-// whole team per heavy vertex (dense counters over the partition).  A step
-// after which nothing remains in the partition does no updates: they could
-// reach no remaining vertex.
+// vertices - a warp per vertex with few wedges in G_p (shared hash); when a
+// step has many heavier ones, 128-thread groups with shared hashes, then (in a
+// cluster) single blocks with larger hashes, take those that fit; the whole
+// team takes the rest (dense counters over the partition).  A step after
+// which nothing remains in the partition does no updates: they could reach no
+// remaining vertex.
 template <class Team>
 __device__ void tip_fd_run(const FDArgs &A, const Team &T, uint32_t cap, uint8_t *sm, size_t warp_bytes,
-                           FMid<FT> &bmb, uint32_t *dense, const BlockGrp<FT> &bg) {
+                           FMid<FT> &bmb, uint32_t *dense, uint8_t *gsm, const BlockGrp<FT> &bg) {
   constexpr bool CL = Team::kCluster;
   FDShared *S = T.S;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -990,7 +1037,7 @@ __device__ void tip_fd_run(const FDArgs &A, const Team &T, uint32_t cap, uint8_t
       S->level = 0;
     }
     long long t_part = clock64();
-    ull p_steps = 0, cyc[3] = {0, 0, 0}, rescans = 0, nbigs = 0;
+    ull p_steps = 0, cyc[3] = {0, 0, 0}, rescans = 0, nbigs = 0, nblkv = 0, nteamv = 0;
     T.sync();
     for (;;) {
       if (*(volatile uint32_t *)&S->na + *(volatile uint32_t *)&S->nc == 0) break;
@@ -1056,8 +1103,68 @@ __device__ void tip_fd_run(const FDArgs &A, const Team &T, uint32_t cap, uint8_t
       // block r of the team walks neighbour chunks r, r + size, ...
       const uint32_t nbig = *(volatile uint32_t *)&S->ncq;
       nbigs += nbig;
-      for (uint32_t bi = 0; bi < nbig; bi++) {
-        const uint32_t x = ldt(&lbig[bi]);
+      uint32_t nteam = nbig;
+      const uint32_t *lteam = lbig;
+      if (nbig >= FG_MIN_BIG) {
+        // many heavy vertices: 128-thread groups (four per block, named
+        // barriers 1-4) take one each with a 2K-slot hash in the dense
+        // counters' memory (zero between uses); heavier ones are listed
+        const int sub = threadIdx.x / FGT;
+        uint8_t *gb = gsm + sub * fd_group_bytes();
+        FMid<FGT> &gmb = *(FMid<FGT> *)gb;
+        uint32_t *gws = (uint32_t *)(gb + align16(sizeof(FMid<FGT>)));
+        SubGrp<FGT> sg{sub * FGT, 1 + sub, gws, nullptr};
+        unsigned long long *gslot = (unsigned long long *)dense + (size_t)sub * FG_CAP;
+        uint32_t *lhuge = A.buf_huge + base;
+        for (;;) {
+          if (sg.rank() == 0) gws[FGT / 32 + 1] = atomicAdd(&S->ng, 1u);
+          sg.sync();
+          const uint32_t k = gws[FGT / 32 + 1];
+          sg.sync();
+          if (k >= nbig) break;
+          const uint32_t x = ldt(&lbig[k]);
+          const uint32_t W = A.w_fd[x];
+          if (W > FG_MAXW) {
+            if (sg.rank() == 0) lhuge[atomicAdd(&S->nh, 1u)] = x;
+            continue;
+          }
+          if (sg.rank() == 0) my_wedges += W;
+          my_updates += fd_hash_vertex(A, sg, gmb, p, x, W, gslot, &S->nc, cand, hi);
+        }
+        T.sync();
+        nteam = *(volatile uint32_t *)&S->nh;
+        lteam = lhuge;
+        if (CL && nteam >= 2) {
+          // a cluster: its blocks take the vertices left one each (8K-slot
+          // hash over the block's dense counters) with block barriers only;
+          // the heaviest go on to the whole team, listed in lbig (read in
+          // full by now)
+          __shared__ uint32_t blk_k;
+          for (;;) {
+            if (threadIdx.x == 0) blk_k = atomicAdd(&S->nbq, 1u);
+            __syncthreads();
+            const uint32_t k = blk_k;
+            __syncthreads();
+            if (k >= nteam) break;
+            const uint32_t x = ldt(&lhuge[k]);
+            const uint32_t W = A.w_fd[x];
+            if (W > FB_MAXW) {
+              if (threadIdx.x == 0) lbig[atomicAdd(&S->nbh, 1u)] = x;
+              continue;
+            }
+            if (threadIdx.x == 0) my_wedges += W;
+            my_updates += fd_hash_vertex(A, bg, bmb, p, x, W, (unsigned long long *)dense, &S->nc, cand, hi);
+          }
+          T.sync();
+          const uint32_t nleft = *(volatile uint32_t *)&S->nbh;
+          nblkv += nteam - nleft;
+          nteam = nleft;
+          lteam = lbig;
+        }
+      }
+      nteamv += nteam;
+      for (uint32_t bi = 0; bi < nteam; bi++) {
+        const uint32_t x = ldt(&lteam[bi]);
         const uint32_t xo = A.p_off[x], xd = A.seg_n[x];
         if (T.leader()) my_wedges += A.w_fd[x];
         if (xd <= csize * FT) {
@@ -1146,13 +1253,17 @@ __device__ void tip_fd_run(const FDArgs &A, const Team &T, uint32_t cap, uint8_t
       T.sync();
       cyc[2] += clock64() - t2;
     }
-    if (T.leader() && A.pstat) {  // steps, cycles; then select, warp path, team path, rescans, heavy vertices
+    if (T.leader() && A.pstat) {
+      // steps, cycles; then select, warp path, heavy-vertex path; rescans;
+      // heavy vertices, those taken by single blocks, by the whole team
       ull *ps = A.pstat + (size_t)TFD_PSTAT * p;
       ps[0] = p_steps;
       ps[1] = (ull)(clock64() - t_part);
       for (int k = 0; k < 3; k++) ps[2 + k] = cyc[k];
       ps[5] = rescans;
       ps[6] = nbigs;
+      ps[7] = nblkv;
+      ps[8] = nteamv;
     }
   }
   my_wedges = bg.sum64(my_wedges);
@@ -1165,7 +1276,7 @@ __device__ void tip_fd_run(const FDArgs &A, const Team &T, uint32_t cap, uint8_t
 }
 
 // one block per partition
-__global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size_t dense_off, uint32_t cap) {
+__global__ void __launch_bounds__(FT, 1) k_fd_tip(FDArgs A, size_t warp_bytes, size_t dense_off, uint32_t cap) {
   extern __shared__ __align__(16) uint8_t sm[];
   __shared__ FDShared S;
   __shared__ TeamMin tmin;
@@ -1173,12 +1284,13 @@ __global__ void __launch_bounds__(FT) k_fd_tip(FDArgs A, size_t warp_bytes, size
   __shared__ ull ws64[FT / 32];
   BlockGrp<FT> bg{ws, ws64};
   BlockTeam T{&S, S.hist, &tmin};
-  tip_fd_run(A, T, cap, sm, warp_bytes, *(FMid<FT> *)(sm + FW * warp_bytes), (uint32_t *)(sm + dense_off), bg);
+  tip_fd_run(A, T, cap, sm, warp_bytes, *(FMid<FT> *)(sm + FW * warp_bytes), (uint32_t *)(sm + dense_off),
+             sm + dense_off + P_DENSE * 4, bg);
 }
 
 // one thread-block cluster per heavy partition (step state in the first
 // block's shared memory, dense counters spread over the blocks)
-__global__ void __launch_bounds__(FT) k_fd_tip_cluster(FDArgs A, size_t warp_bytes, size_t dense_off, uint32_t cap) {
+__global__ void __launch_bounds__(FT, 1) k_fd_tip_cluster(FDArgs A, size_t warp_bytes, size_t dense_off, uint32_t cap) {
   extern __shared__ __align__(16) uint8_t sm[];
   __shared__ FDShared S;
   __shared__ TeamMin tmin;
@@ -1188,12 +1300,13 @@ __global__ void __launch_bounds__(FT) k_fd_tip_cluster(FDArgs A, size_t warp_byt
   BlockGrp<FT> bg{ws, ws64};
   cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
   ClusterTeam T{cl.map_shared_rank(&S, 0), lhist, &tmin, cl.block_rank(), cl.num_blocks()};
-  tip_fd_run(A, T, cap, sm, warp_bytes, *(FMid<FT> *)(sm + FW * warp_bytes), (uint32_t *)(sm + dense_off), bg);
+  tip_fd_run(A, T, cap, sm, warp_bytes, *(FMid<FT> *)(sm + FW * warp_bytes), (uint32_t *)(sm + dense_off),
+             sm + dense_off + P_DENSE * 4, bg);
 }
 
 size_t fd_warp_bytes() { return align16(PW_CAP * 8 + sizeof(FMid<32>)); }
 size_t fd_dense_off() { return align16(FW * fd_warp_bytes() + sizeof(FMid<FT>)); }
-size_t fd_smem() { return fd_dense_off() + P_DENSE * 4; }
+size_t fd_smem() { return fd_dense_off() + P_DENSE * 4 + (FT / FGT) * fd_group_bytes(); }
 
 // FD adjacency keys: (y, part(x)) for every Y-side entry
 __global__ void k_fd_keys(const uint32_t *o_off, const uint32_t *o_adj0, uint32_t ny, const uint32_t *part, int bp,
@@ -1770,6 +1883,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   F.buf_d = a.alloc<uint32_t>(nx);
   F.buf_f = front;
   F.buf_big = front2;
+  F.buf_huge = a.alloc<uint32_t>(nx);
   F.gcnt = a.zeros<uint32_t>(nx);
   F.queue = dc + 8;
   F.wedges = dwedge + 6;
@@ -1834,11 +1948,12 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
     std::vector<uint32_t> hps(nparts + 1);
     CK(cudaMemcpy(pst.data(), pstat, pst.size() * 8, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(hps.data(), ps, hps.size() * 4, cudaMemcpyDeviceToHost));
-    // side partition |X_p| work steps cycles | cycles of select, warp path, team path | rescans heavy-vertices
+    // side partition |X_p| work steps cycles | cycles of select, warp path, heavy path | rescans
+    // heavy-vertices (of which by single blocks, by the whole team)
     for (uint32_t i = 0; i < nparts; i++) {
       const ull *q = &pst[(size_t)TFD_PSTAT * i];
-      fprintf(trace, "F %d %u %u %llu %llu %llu %llu %llu %llu %llu %llu\n", side, i, hps[i + 1] - hps[i],
-              (unsigned long long)hwork[i], q[0], q[1], q[2], q[3], q[4], q[5], q[6]);
+      fprintf(trace, "F %d %u %u %llu %llu %llu %llu %llu %llu %llu %llu %llu %llu\n", side, i, hps[i + 1] - hps[i],
+              (unsigned long long)hwork[i], q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8]);
     }
   }
   if (st) {

@@ -864,6 +864,40 @@ void be_index_sums(Arena &a, const Graph &G, uint64_t *out_e, uint64_t *total, p
 }
 
 // --------------------------------------------------------------- driver
+namespace {
+// warp per U vertex: min(d_u, d_v) for each of its edges
+__global__ void k_edge_min_deg(const uint32_t *u_off, const uint32_t *u_adj, const uint32_t *v_off, uint32_t nu,
+                               uint32_t *out) {
+  const int lane = threadIdx.x & 31;
+  size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5, nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t u = gw; u < nu; u += nw) {
+    const uint32_t o = u_off[u], du = u_off[u + 1] - o;
+    for (uint32_t k = lane; k < du; k += 32) {
+      const uint32_t v = u_adj[o + k];
+      out[o + k] = min(du, v_off[v + 1] - v_off[v]);
+    }
+  }
+}
+
+// work proxy (support) of the remaining edges with support below a bound
+__global__ void k_wing_work_below(const uint32_t *alist, uint32_t na, const ull *sup, ull bound, ull *out) {
+  ull s = 0;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < na; j += (size_t)gridDim.x * blockDim.x) {
+    const ull v = sup[alist[j]];
+    if (v < bound) s += v;
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+}  // namespace
+
+void edge_min_degrees(Arena &a, const Graph &G, uint32_t *out) {
+  if (!G.m) return;
+  const int T = 256;
+  k_edge_min_deg<<<grid_for((size_t)G.nu * 32, T, 16 * num_sms()), T, 0, a.st>>>(G.u_off, G.u_adj, G.v_off, G.nu, out);
+  CK_LAUNCH();
+}
+
 void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_out, pbng_stats *st) {
   const int T = 256;
   const int sms = num_sms();
@@ -925,6 +959,23 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
   A.touched_n = dc + 2;
   A.ctr = wctr;
 
+  // learned bounds: features of the initial supports and edge degrees ->
+  // MLP -> bounds, each judged by the estimator in its range
+  std::vector<uint64_t> learned;
+  const uint64_t *bounds = prm.bounds;
+  uint32_t n_bounds = prm.bounds_mode == PBNG_BOUNDS_EXPLICIT ? prm.n_bounds : 0;
+  const bool is_learned = prm.bounds_mode == PBNG_BOUNDS_LEARNED;
+  if (is_learned) {
+    float *feat = a.alloc<float>(128);
+    uint32_t *edeg = a.alloc<uint32_t>(m);
+    edge_min_degrees(a, G, edeg);
+    const uint64_t K = bound_features(a, (const uint64_t *)sup, nullptr, m, feat, edeg);
+    learned = propose_bounds(a, prm.mlp_params, prm.mlp_hidden, prm.mlp_out, feat, K);
+    a.free(edeg);
+    a.free(feat);
+    bounds = learned.data();
+    n_bounds = (uint32_t)learned.size();
+  }
   uint32_t na = m, pi = 0, P = prm.P;
   double scale = 1.0;
   uint64_t prev_init_est = 0, rounds = 0, front_total = 0;
@@ -959,9 +1010,22 @@ void wing_decompose(Arena &a, Graph &G, const TipParams &prm, uint64_t *theta_ou
     if (last) {
       thi = ~0ull;
       use_est = false;
-    } else if (prm.bounds_mode == PBNG_BOUNDS_EXPLICIT && pi < prm.n_bounds && prm.bounds[pi] > kmin) {
-      thi = prm.bounds[pi];
+    } else if (pi < n_bounds && bounds[pi] > kmin) {
+      thi = bounds[pi];
       use_est = false;
+      if (is_learned && prm.learned_vet > 0 && wsum > 0) {
+        // the plain estimator judges a learned bound: its range may hold at
+        // most learned_vet times the estimator's target work
+        const double t = (double)wsum * scale / (double)(P - pi);
+        ull *d = a.zeros<ull>(1), wb = 0;
+        k_wing_work_below<<<grid_for(na, T, cap), T, 0, a.st>>>(alist, na, sup, thi, d);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(&wb, d, 8, cudaMemcpyDeviceToHost, a.st));
+        CK(cudaStreamSynchronize(a.st));
+        a.free(d);
+        if ((double)wb > prm.learned_vet * std::max(t, 1.0)) use_est = true;
+        else init_est = wb;
+      }
     }
     if (use_est) {
       if (wsum == 0 || kmin == kmax) {

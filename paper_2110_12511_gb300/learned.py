@@ -14,6 +14,11 @@ and blends of the two in log space), each is timed on the GPU, and the
 fastest becomes the target.  Any bounds give identical tip numbers (Sec. 4.1,
 Th. 2), so the network can only change speed; a bound that would peel nothing
 falls back to find_range inside the library.
+
+The wing proposer is the same network over the edges
+(``pbng_wing_bound_features``: min(d_u, d_v) per edge and the per-edge
+initial butterfly counts), with work quantiles taken over the exact wing
+numbers weighted by support, the wing work proxy (Sec. 3.3.2).
 """
 from __future__ import annotations
 
@@ -22,11 +27,14 @@ import time
 
 import numpy as np
 
-from . import BOUNDS_ESTIMATOR, as_u64, bound_features, mlp_adam, mlp_grad, tip_decompose, to_device
+from . import (BOUNDS_ESTIMATOR, as_u64, bound_features, mlp_adam, mlp_grad, tip_decompose, to_device,
+               wing_bound_features, wing_decompose)
 
 NIN, HID = 128, 128
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "data", "bound_mlp_p200.npz")
+WING_WEIGHTS = os.path.join(HERE, "data", "bound_mlp_wing_p100.npz")
+BLENDS = (0.25, 0.5, 0.75)
 
 
 def n_params(nin=NIN, hid=HID, out=199):
@@ -92,8 +100,32 @@ def blend(a, b, t, P):
     return np.array(out, dtype=np.uint64)
 
 
-def training_example(g, side, P, reps=2):
-    """(features, target y, info) for one graph: the fastest candidate bounds."""
+def _fastest(run, cands, reps):
+    """Name of the fastest candidate: run(bounds or None) timed on the GPU."""
+    import torch
+    times = {}
+    for name, b in cands.items():
+        best = 1e30
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            run(b if name != "estimator" else None)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        times[name] = best
+    return min(times, key=times.get), times
+
+
+def candidates(est, wq, P):
+    c = {"estimator": est, "work_quantiles": wq}
+    for t in BLENDS:
+        c[f"blend_{t}"] = blend(est, wq, t, P)
+    return c
+
+
+def training_example(g, side, P, reps=2, graph_rounds=True):
+    """(features, target y, info) for one graph: the fastest candidate bounds
+    (timed as the decomposition runs by default: graph-captured rounds)."""
     import torch
     from . import count
     dg = to_device(g)
@@ -109,19 +141,25 @@ def training_example(g, side, P, reps=2):
     do = np.bincount(h.u_adj, minlength=h.nv).astype(np.float64)
     w = np.bincount(np.repeat(np.arange(h.nu), dh), weights=do[h.u_adj], minlength=h.nu)
     wq = quantile_bounds(theta, w, P)
-    cands = {"estimator": est, "work_quantiles": wq, "blend_0.25": blend(est, wq, 0.25, P),
-             "blend_0.5": blend(est, wq, 0.5, P)}
-    times = {}
-    for name, b in cands.items():
-        best = 1e30
-        for _ in range(reps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            tip_decompose(dg, side, P=P, bounds=b if name != "estimator" else None)
-            torch.cuda.synchronize()
-            best = min(best, time.perf_counter() - t0)
-        times[name] = best
-    win = min(times, key=times.get)
+    cands = candidates(est, wq, P)
+    win, times = _fastest(lambda b: tip_decompose(dg, side, P=P, bounds=b, graph_rounds=graph_rounds), cands, reps)
+    return feat, encode(cands[win], P - 1, K), {"times": times, "winner": win, "K": K}
+
+
+def wing_training_example(g, P, reps=2):
+    """(features, target y, info) for the wing proposer on one graph."""
+    from . import count
+    dg = to_device(g)
+    feat = wing_bound_features(dg).cpu().numpy()
+    _, _, ce = count(dg, vertices=False, edges=True)
+    sup = as_u64(ce).astype(np.float64)
+    K = int(sup.max()) if sup.size else 0
+    used = np.zeros(P, dtype=np.uint64)
+    theta, st = wing_decompose(dg, P=P, with_stats=True, bounds_out=used)
+    est = used[:max(st["parts_used"] - 1, 0)].copy()
+    wq = quantile_bounds(as_u64(theta).astype(np.float64), sup, P)
+    cands = candidates(est, wq, P)
+    win, times = _fastest(lambda b: wing_decompose(dg, P=P, bounds=b), cands, reps)
     return feat, encode(cands[win], P - 1, K), {"times": times, "winner": win, "K": K}
 
 
@@ -158,7 +196,8 @@ def save(path, params, out, meta=None):
 
 
 def load(path=DEFAULT_WEIGHTS, device="cuda"):
-    """(params tensor on device, hidden, out) ready for tip_decompose(mlp=...)."""
+    """(params tensor on device, hidden, out) ready for tip_decompose(mlp=...)
+    (or wing_decompose(mlp=...) with WING_WEIGHTS)."""
     import torch
     d = np.load(path)
     return torch.as_tensor(d["params"], device=device).contiguous(), int(d["hidden"]), int(d["out"])

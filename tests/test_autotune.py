@@ -5,7 +5,8 @@ from paper_2110_12511_gb300 import autotune as at
 
 def test_coordinate_search_finds_separable_optimum():
     # a separable cost: each knob has one best value; the search must find all of them
-    best_vals = {"graph_rounds": True, "warp_max_w": 256, "group_max_w": 1024, "item_w": 131072, "bucket_shift": 16}
+    best_vals = {"graph_rounds": True, "warp_max_w": 256, "group_max_w": 1024, "item_w": 131072, "bucket_shift": 16,
+                 "count_scratch": 1, "fd_cluster_min": 8192}
 
     def measure(cfg):
         return 1.0 + sum(0.1 for k, v in best_vals.items() if cfg.get(k) != v)
@@ -36,6 +37,9 @@ def test_valid_and_split():
     assert not at.valid({"warp_max_w": 256, "group_max_w": 128})
     assert not at.valid({"item_w": 1000})
     assert not at.valid({"bucket_shift": 12})
-    kw = at.split({"graph_rounds": True, "warp_max_w": 128, "item_w": 8192, "bucket_shift": 16})
+    assert not at.valid({"count_scratch": 4})
+    kw = at.split({"graph_rounds": True, "warp_max_w": 128, "item_w": 8192, "bucket_shift": 16, "count_scratch": 2,
+                   "fd_cluster_min": 8192})
     assert kw == {"graph_rounds": True, "bucket_shift": 16,
-                  "schedule": {"warp_max_w": 128, "group_max_w": 0, "item_w": 8192}}
+                  "schedule": {"warp_max_w": 128, "group_max_w": 0, "item_w": 8192, "count_scratch": 2,
+                               "fd_cluster_min": 8192}}

@@ -10,8 +10,9 @@ import oracle
 from oracle import mlp as omlp
 
 pytestmark = pytest.mark.gpu
-WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2110_12511_gb300", "data",
-                       "bound_mlp_p200.npz")
+DATA = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2110_12511_gb300", "data")
+WEIGHTS = os.path.join(DATA, "bound_mlp_p200.npz")
+WING_WEIGHTS = os.path.join(DATA, "bound_mlp_wing_p100.npz")
 
 
 @pytest.fixture(scope="module")
@@ -90,6 +91,44 @@ def test_features_match_oracle_counts(pbng):
         assert np.allclose(f[:64], fd, atol=1e-6) and np.allclose(f[64:], fs, atol=1e-6)
 
 
+def test_wing_features_match_oracle_counts(pbng):
+    """Wing features: min(d_u, d_v) per edge and the oracle's per-edge counts."""
+    g = gen.make("chunglu_5k_1k_50k_planted")
+    f = pbng.wing_bound_features(pbng.to_device(g)).cpu().numpy()
+    du = np.diff(g.u_off).astype(np.int64)
+    dv = np.bincount(g.u_adj, minlength=g.nv).astype(np.int64)
+    eu = np.repeat(np.arange(g.nu), du)
+    deg = np.minimum(du[eu], dv[g.u_adj])
+    cnt = oracle.edge_counts(g)
+    fd = np.bincount(half_octave(deg), minlength=64)[:64] / g.m
+    bl = np.array([int(c).bit_length() for c in cnt])
+    fs = np.bincount(np.minimum(bl.max() - bl, 63), minlength=64)[:64] / g.m
+    assert np.allclose(f[:64], fd, atol=1e-6) and np.allclose(f[64:], fs, atol=1e-6)
+
+
+def wing_mlp():
+    import torch
+    from paper_2110_12511_gb300 import learned
+    if os.path.exists(WING_WEIGHTS):
+        return learned.load(WING_WEIGHTS)
+    return torch.as_tensor(learned.init_params(99, 2), device="cuda"), 128, 99
+
+
+@pytest.mark.parametrize("vet", [0.0, -1.0])
+@pytest.mark.parametrize("name", ["chunglu_5k_1k_50k_planted", "rand_dense"])
+def test_learned_wing_bounds_give_identical_wing_numbers(pbng, name, vet):
+    """Learned wing bounds, judged by the estimator or not: the oracle's wing
+    numbers (Th. 2), and the bounds reported are strictly increasing."""
+    g = gen.make(name) if name != "rand_dense" else gen.uniform(60, 50, 1500, 9)
+    dg = pbng.to_device(g)
+    used = np.zeros(100, dtype=np.uint64)
+    th, st = pbng.wing_decompose(dg, P=100, mlp=wing_mlp(), learned_vet=vet, with_stats=True, bounds_out=used)
+    assert np.array_equal(pbng.as_u64(th), oracle.wing(g))
+    b = used[:np.count_nonzero(used)]
+    assert b.size in (st["parts_used"] - 1, st["parts_used"])
+    assert (np.diff(b.astype(np.float64)) > 0).all()
+
+
 def test_training_reduces_loss(pbng):
     from paper_2110_12511_gb300 import learned
     rng = np.random.default_rng(4)
@@ -163,7 +202,7 @@ def test_learned_bounds_gain_on_heldout_graph(pbng):
     if not os.path.exists(WEIGHTS):
         pytest.skip("no trained weights")
     mlp = learned.load(WEIGHTS)
-    g = train_bounds.training_graph(1000, 500000, 20000000)
+    g = train_bounds.training_graph(1000, 1000000, 60000000)
     dg = pbng.to_device(g)
     def run(m):
         best, res = 1e30, None

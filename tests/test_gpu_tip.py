@@ -265,7 +265,8 @@ def test_malformed_csr_is_rejected(pbng):
 
 @pytest.mark.parametrize("knob,value", [("warp_max_w", 1), ("warp_max_w", 128), ("group_max_w", 512),
                                         ("item_w", 4096), ("item_w", 1 << 30), ("bucket_shift", 14), ("bucket_shift", 16),
-                                        ("graph_rounds", True)])
+                                        ("graph_rounds", True), ("count_scratch", 1), ("count_scratch", 2),
+                                        ("fd_cluster_min", 8192), ("fd_cluster_min", 0xFFFFFFFF)])
 def test_tip_every_schedule_variant(pbng, knob, value):
     """Every value the autotuner may choose, forced once: identical tip numbers."""
     from paper_2110_12511_gb300 import autotune as at
@@ -379,6 +380,48 @@ def test_tip_cluster_fine_phase_global_counters(pbng):
     got, st = pbng.tip_decompose(dg, "U", P=1, schedule={"fd_cluster_min": 1}, with_stats=True)
     assert st["parts_used"] == 1
     assert np.array_equal(pbng.as_u64(got), oracle.tip(g, "U"))
+
+
+def tier_graph():
+    """Disjoint bicliques: the U vertices of each size tie, so one fine-phase
+    step peels all of them, with in-partition wedge counts of 380 (128-thread
+    groups take them), 1,560 and 3,540 (single blocks of a cluster) and 5,960
+    (the whole cluster); the last step (K_80,80) makes no updates.  Plus a
+    sparse random part on vertices of its own."""
+    rng = np.random.default_rng(77)
+    eu, ev, u0, v0 = [], [], 0, 0
+    for a, b in ((20, 20), (20, 20), (40, 40), (40, 40), (40, 40), (60, 60), (60, 60), (150, 40), (80, 80)):
+        eu.append(np.repeat(np.arange(u0, u0 + a), b))
+        ev.append(np.tile(np.arange(v0, v0 + b), a))
+        u0, v0 = u0 + a, v0 + b
+    eu.append(u0 + rng.integers(0, 300, 1500))
+    ev.append(v0 + rng.integers(0, 100, 1500))
+    return gen.from_edges(u0 + 300, v0 + 100, np.concatenate(eu), np.concatenate(ev))
+
+
+@pytest.mark.parametrize("cmin", [1, 0xFFFFFFFF])
+def test_tip_fine_phase_heavy_tiers(pbng, tmp_path, cmin):
+    """A step that peels many heavy vertices at once: 128-thread groups take
+    the lighter ones, then (on a thread-block cluster) single blocks, and the
+    whole team the rest (per the fine-phase trace); one block per partition
+    has no block tier.  Numbers equal the oracle's either way."""
+    import os
+    g = tier_graph()
+    dg = pbng.to_device(g)
+    tr = tmp_path / "trace.txt"
+    os.environ["PBNG_TRACE"] = str(tr)
+    try:
+        got = pbng.tip_decompose(dg, "U", P=1, schedule={"fd_cluster_min": cmin})
+    finally:
+        del os.environ["PBNG_TRACE"]
+    assert np.array_equal(pbng.as_u64(got), oracle.tip(g, "U"))
+    rows = [list(map(int, l.split()[1:])) for l in open(tr) if l.startswith("F ")]
+    assert len(rows) == 1
+    heavy, by_block, by_team = rows[0][-3:]
+    if cmin == 1:
+        assert by_block > 0 and by_team > 0 and heavy > by_block + by_team
+    else:
+        assert by_block == 0 and 0 < by_team < heavy
 
 
 @pytest.mark.parametrize("scratch", [0, 1, 2, 3])
