@@ -73,6 +73,18 @@ struct PeelArgs {
   ull *sup;
   ull *updates;
   uint32_t nx;
+  ull *bstat;  // block-class statistics (BS_*), null unless tracing
+};
+
+// block-class statistics of a round, gathered when tracing in a build with
+// PBNG_PEEL_STATS=1 (off by default: the counters cost registers): items, SM
+// cycles of the phases, passes, wedges, walked lanes, drains
+#ifndef PBNG_PEEL_STATS
+#define PBNG_PEEL_STATS 0
+#endif
+enum {
+  BS_ITEMS = 0, BS_CYC_PLAN, BS_CYC_WALK, BS_CYC_DRAIN, BS_CYC_REWALK, BS_PASS_HASH, BS_PASS_DENSE, BS_WEDGES,
+  BS_LANES, BS_DRAIN_DENSE, BS_DRAIN_SPARSE, BS_CYC_ITEM, BSTAT
 };
 
 // slices of the current lists being walked: start, length, and the
@@ -322,6 +334,18 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
   const uint32_t xo = A.p_off[x], xd = A.p_off[x + 1] - xo, nbi = b1 - b0;
   const int t = threadIdx.x;
   uint64_t nup = 0;
+  const bool stat = PBNG_PEEL_STATS && A.bstat && t == 0;  // (a few global atomics per pass)
+  long long c_item = stat ? clock64() : 0, c_mark = c_item;
+  auto add = [&](int k, ull v) {
+    if (stat) atomicAdd(&A.bstat[k], v);
+  };
+  auto mark = [&](int k) {
+    if (stat) {
+      long long c = clock64();
+      atomicAdd(&A.bstat[k], (ull)(c - c_mark));
+      c_mark = c;
+    }
+  };
   // this thread's neighbour (items of vertices with at most N neighbours)
   const bool cached = xd <= (uint32_t)N;
   uint32_t my_s0 = 0, my_len = 0;
@@ -397,6 +421,7 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
   }
   __syncthreads();
   const uint32_t np = pl.np;
+  mark(BS_CYC_PLAN);
   // 3. passes
   for (uint32_t qi = 0; qi < np; qi++) {
     const uint32_t bs = b0 + pl.a[qi], be = b0 + pl.a[qi + 1], Tq = pl.b[qi];
@@ -442,8 +467,12 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
         }
         return Cw;
       };
+      bool rewalk = false;
+      add(hash ? BS_PASS_HASH : BS_PASS_DENSE, 1);
+      add(BS_WEDGES, Tq);
       if (hash && packed) {
-        walk_all([&](uint32_t xp) { h32.inc(xp); });
+        add(BS_LANES, 32ull * walk_all([&](uint32_t xp) { h32.inc(xp); }));
+        mark(BS_CYC_WALK);
         const uint32_t cmask = (1u << cb) - 1u;
         for (uint32_t i = 4 * t; i < cap; i += 4 * N) {  // drain four slots at a time
           uint4 q = *(uint4 *)&tab[i];
@@ -457,7 +486,8 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
           *(uint4 *)&tab[i] = make_uint4(0u, 0u, 0u, 0u);
         }
       } else if (hash) {
-        walk_all([&](uint32_t xp) { h.inc(xp); });
+        add(BS_LANES, 32ull * walk_all([&](uint32_t xp) { h.inc(xp); }));
+        mark(BS_CYC_WALK);
         for (uint32_t i = 2 * t; i < cap; i += 2 * N) {  // drain two slots at a time
           uint4 q = *(uint4 *)&tab[2 * i];  // slots i, i + 1: (count, tag) words
           if ((q.x | q.y | q.z | q.w) == 0u) continue;
@@ -470,10 +500,15 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
           uint32_t o = xp - d0;
           atomicAdd(&tab[o & (P_CHUNK - 1)], 1u << ((o >> 14) * 16));
         });
+        add(BS_LANES, 32ull * Cw);
+        mark(BS_CYC_WALK);
         const uint64_t Tw = narrow ? (uint64_t)Tq : (uint64_t)Cw * 32;
         if (Tw >= (d1 - d0) / 2 || !cached) {  // crowded (or slices not kept): scan the counters
+          add(BS_DRAIN_DENSE, 1);
           nup += drain_dense<true>(A, tab, d0, d1 - d0, t, N);
         } else {  // sparse: walk the wedges again, the first visitor takes the count
+          add(BS_DRAIN_SPARSE, 1);
+          rewalk = true;
           walk_slices(A, t, mb, (int)xd, Cw, [&](uint32_t xp) {
             uint32_t o = xp - d0, sh = (o >> 14) * 16;
             uint32_t c = (atomicAnd(&tab[o & (P_CHUNK - 1)], ~(0xffffu << sh)) >> sh) & 0xffffu;
@@ -482,10 +517,15 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
         }
       } else {
         const uint32_t Cw = walk_all([&](uint32_t xp) { atomicAdd(&tab[xp - d0], 1u); });
+        add(BS_LANES, 32ull * Cw);
+        mark(BS_CYC_WALK);
         const uint64_t Tw = narrow ? (uint64_t)Tq : (uint64_t)Cw * 32;
         if (Tw >= (d1 - d0) / 2 || !cached) {
+          add(BS_DRAIN_DENSE, 1);
           nup += drain_dense<false>(A, tab, d0, d1 - d0, t, N);
         } else {
+          add(BS_DRAIN_SPARSE, 1);
+          rewalk = true;
           walk_slices(A, t, mb, (int)xd, Cw, [&](uint32_t xp) {
             uint32_t c = atomicExch(&tab[xp - d0], 0u);
             if (c >= 2) sub_support(A, xp, choose2(c)), nup++;
@@ -493,9 +533,12 @@ __device__ uint64_t peel_item_block(const PeelArgs &A, uint32_t x, uint32_t b0, 
         }
       }
       __syncthreads();
+      mark(rewalk ? BS_CYC_REWALK : BS_CYC_DRAIN);
     }
   }
   __syncthreads();  // the plan arrays are rewritten by the next item
+  add(BS_ITEMS, 1);
+  if (stat) add(BS_CYC_ITEM, (ull)(clock64() - c_item));
   return nup;
 }
 
@@ -1482,6 +1525,7 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
   PA.sup = sup;
   PA.updates = dwedge + 8;
   PA.nx = nx;
+  PA.bstat = trace && PBNG_PEEL_STATS ? a.zeros<ull>(BSTAT) : nullptr;
 
   static bool attr = false;
   size_t wsm = (PWT / 32) * align16(QW_CAP * 8 + sizeof(PMid<32>));
@@ -1808,6 +1852,14 @@ void tip_decompose(Arena &a, Graph &G, int side, const TipParams &prm, uint64_t 
         fprintf(trace, "%d %u %llu %u %u %u %u %llu %llu %d %.4f %.4f %.4f %.4f %.4f %.4f %.4f %.4f\n", side, pi,
                 (unsigned long long)rounds, nf, hc[2 + PC_WARP], hc[2 + PC_GROUP], hc[2 + PC_BLOCK], hw, hw2[2],
                 (int)do_recount, ms, m1, m2, ms - m1 - m2, mp, mc, mf, wall);
+        if (PA.bstat && !do_recount && hc[2 + PC_BLOCK]) {  // block class: "B" side range round, then BS_*
+          ull hb[BSTAT];
+          CK(cudaMemcpy(hb, PA.bstat, sizeof(hb), cudaMemcpyDeviceToHost));
+          CK(cudaMemset(PA.bstat, 0, sizeof(hb)));
+          fprintf(trace, "B %d %u %llu", side, pi, (unsigned long long)rounds);
+          for (int k = 0; k < BSTAT; k++) fprintf(trace, " %llu", hb[k]);
+          fprintf(trace, "\n");
+        }
       }
       nf = nf_next;
       std::swap(front, front2);
