@@ -53,3 +53,25 @@ def test_signature_depends_on_sizes_and_degrees():
     assert at.signature(g1, "U", 10) != at.signature(g1, "V", 10)
     assert at.signature(g1, "U", 10) != at.signature(g1, "U", 20)
     assert at.signature(g1, "U", 10) == at.signature(G([0, 2, 4, 8], 5), "U", 10)
+
+
+def test_candidates_cover_estimator_quantiles_and_blends():
+    est = np.array([5, 50, 500], dtype=np.uint64)
+    wq = np.array([20, 2000, 20000], dtype=np.uint64)
+    c = learned.candidates(est, wq, 4)
+    assert set(c) == {"estimator", "work_quantiles", "blend_0.25", "blend_0.5", "blend_0.75"}
+    # blends move monotonically from the estimator's bounds towards the quantiles
+    logs = [np.log2(1 + c[k].astype(np.float64)).mean() for k in ("blend_0.25", "blend_0.5", "blend_0.75")]
+    assert logs[0] < logs[1] < logs[2]
+
+
+def test_training_recipes_are_seeded_and_in_range():
+    from paper_2110_12511_gb300 import train_bounds as tb
+    g1 = tb.training_wing_graph(3, 20000, 40000)
+    g2 = tb.training_wing_graph(3, 20000, 40000)
+    assert np.array_equal(g1.u_off, g2.u_off) and np.array_equal(g1.u_adj, g2.u_adj)
+    # base edges in range, plus at most 200 planted bicliques of up to 200 x 200
+    assert 20000 * 0.9 <= g1.m <= 40000 + 200 * 200 * 200
+    assert g1.nu >= 2000 and g1.nv >= 400
+    t = tb.training_graph(1, 20000, 40000)
+    assert 10000 <= t.m <= 40000 and t.nu + t.nv <= 4000 + 2
