@@ -105,7 +105,7 @@ struct HashPolicy {
   __device__ void inc(uint32_t k) const { h.inc(k); }
   __device__ uint32_t get(uint32_t k) const { return h.get(k); }
   template <class Grp, int N>
-  __device__ uint64_t drain(const CArgs &A, uint32_t, uint32_t, uint32_t, bool sl, const Grp &g, MidBuf<N> &,
+  __device__ uint64_t drain(const CArgs &A, uint32_t, uint32_t, uint32_t, bool sl, const Grp &g, MidBuf<N> &, uint32_t,
                             uint64_t &nat, uint64_t &nb, uint64_t &np) const {
     uint64_t ss = 0;
     for (uint32_t i = g.rank(); i < cap; i += N) {
@@ -132,7 +132,7 @@ struct DensePolicy {  // counters for labels [0, s) in shared memory
   __device__ void inc(uint32_t k) const { atomicAdd(&c[k], 1u); }
   __device__ uint32_t get(uint32_t k) const { return c[k]; }
   template <class Grp, int N>
-  __device__ uint64_t drain(const CArgs &A, uint32_t s, uint32_t, uint32_t, bool sl, const Grp &g, MidBuf<N> &,
+  __device__ uint64_t drain(const CArgs &A, uint32_t s, uint32_t, uint32_t, bool sl, const Grp &g, MidBuf<N> &, uint32_t,
                             uint64_t &nat, uint64_t &nb, uint64_t &np) const {
     uint64_t ss = 0;
     for (uint32_t i = g.rank(); i < s; i += N) {
@@ -156,12 +156,13 @@ struct GlobalPolicy {  // per-block dense counters over all labels in global mem
   uint32_t *c;
   __device__ void inc(uint32_t k) const { atomicAdd(&c[k], 1u); }
   __device__ uint32_t get(uint32_t k) const { return __ldcg(&c[k]); }
+  // C1: the chunk count of the slices still in mb when all mids fit one load
   template <class Grp, int N>
   __device__ uint64_t drain(const CArgs &A, uint32_t s, uint32_t so, uint32_t sd, bool sl, const Grp &g,
-                            MidBuf<N> &mb, uint64_t &nat, uint64_t &nb, uint64_t &np) const {
+                            MidBuf<N> &mb, uint32_t C1, uint64_t &nat, uint64_t &nb, uint64_t &np) const {
     uint64_t ss = 0;
     for (uint32_t base = 0; base < sd; base += N) {
-      uint32_t C = load_mids(A, s, so, sd, base, g, mb);
+      uint32_t C = sd <= (uint32_t)N ? C1 : load_mids(A, s, so, sd, base, g, mb);
       walk(A, g, mb, sd, base, C, [&](int, uint32_t, uint32_t last) {
         if (A.alive && !A.alive[last]) return;
         uint32_t x = atomicExch(&c[last], 0u);  // first visitor of last takes its count
@@ -180,19 +181,39 @@ struct GlobalPolicy {  // per-block dense counters over all labels in global mem
 };
 
 // end of one start: s gains the sum of C(wc, 2) over its lasts, the
-// BE-Index sizes of s, and the counters (sums over the group)
-template <class Grp>
+// BE-Index sizes of s, and the counters.  The five sums of the group are
+// formed in one round: warp shuffles, then (groups of several warps) shared
+// 64-bit atomics into mb.acc[0..4], which is zero between passes and is left
+// zero; one barrier.  The caller's last barrier (after the drain) already
+// orders the table for the next start.
+template <class Grp, int N>
 __device__ void count_finish(const CArgs &A, uint32_t s, uint32_t sd, bool sl, uint64_t ss, uint64_t wc, uint64_t nat,
-                             uint64_t nb, uint64_t np, const Grp &g) {
-  uint64_t tot = g.sum64(ss), wt = g.sum64(wc), at = g.sum64(nat);
-  if (A.be_nb) {
-    uint64_t tb = g.sum64(nb), tp = g.sum64(np);
-    if (g.rank() == 0) {
+                             uint64_t nb, uint64_t np, const Grp &g, MidBuf<N> &mb) {
+  uint64_t v[5] = {ss, wc, nat, nb, np};
+#pragma unroll
+  for (int k = 0; k < 5; k++)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if constexpr (N > 32) {
+    if ((g.rank() & 31) == 0)
+#pragma unroll
+      for (int k = 0; k < 5; k++)
+        if (v[k]) atomicAdd(&mb.acc[k], (unsigned long long)v[k]);
+    g.sync();
+    if (g.rank() == 0)
+#pragma unroll
+      for (int k = 0; k < 5; k++) {
+        v[k] = mb.acc[k];
+        mb.acc[k] = 0;
+      }
+  }
+  if (g.rank() == 0) {
+    const uint64_t tot = v[0], wt = v[1], tb = v[3], tp = v[4];
+    uint64_t at = v[2];
+    if (A.be_nb) {
       A.be_nb[s] = tb;
       A.be_np[s] = tp;
     }
-  }
-  if (g.rank() == 0) {
     if (sl && tot) atomicAdd(&A.cnt[s], (unsigned long long)tot), at++;
     if (A.ctr) {
       if (wt) atomicAdd(&A.ctr[0], (unsigned long long)wt);
@@ -200,7 +221,7 @@ __device__ void count_finish(const CArgs &A, uint32_t s, uint32_t sd, bool sl, u
       if (at) atomicAdd(&A.ctr[2], (unsigned long long)at);
     }
   }
-  g.sync();
+  if constexpr (N == 32) g.sync();
 }
 
 template <class Grp, int N, class Tbl>
@@ -209,9 +230,12 @@ __device__ void count_start(const CArgs &A, uint32_t s, const Grp &g, MidBuf<N> 
   bool sl = want(A, s);
   bool md = A.want_side < 0 || !sl;
   uint64_t wc = 0, nat = 0;
+  // a start whose mids fit one load keeps its slices in mb for passes 2-3
+  uint32_t C1 = 0;
   // pass 1: wedge_count[last]++ for every valid wedge (Alg. 1 l.9-13)
   for (uint32_t base = 0; base < sd; base += N) {
     uint32_t C = load_mids(A, s, so, sd, base, g, mb);
+    C1 = C;
     walk(A, g, mb, sd, base, C, [&](int, uint32_t, uint32_t last) {
       if (A.alive && !A.alive[last]) return;
       tbl.inc(last);
@@ -223,7 +247,7 @@ __device__ void count_start(const CArgs &A, uint32_t s, const Grp &g, MidBuf<N> 
   // (Alg. 1 l.18-19 and l.21-23)
   if (md || A.cnt_e) {
     for (uint32_t base = 0; base < sd; base += N) {
-      uint32_t C = load_mids(A, s, so, sd, base, g, mb);
+      uint32_t C = sd <= (uint32_t)N ? C1 : load_mids(A, s, so, sd, base, g, mb);
       walk(A, g, mb, sd, base, C, [&](int i, uint32_t pos, uint32_t last) {
         if (A.alive && !A.alive[last]) return;
         uint32_t c = tbl.get(last);
@@ -245,9 +269,9 @@ __device__ void count_start(const CArgs &A, uint32_t s, const Grp &g, MidBuf<N> 
   }
   // pass 3: start and last gain C(wc, 2) (Alg. 1 l.15-17); clears the table
   uint64_t nb = 0, np = 0;
-  uint64_t ss = tbl.drain(A, s, so, sd, sl, g, mb, nat, nb, np);
+  uint64_t ss = tbl.drain(A, s, so, sd, sl, g, mb, C1, nat, nb, np);
   g.sync();
-  count_finish(A, s, sd, sl, ss, wc, nat, nb, np, g);
+  count_finish(A, s, sd, sl, ss, wc, nat, nb, np, g, mb);
 }
 
 // the slices of the mids in [base, base + N) holding lasts with labels in
@@ -358,7 +382,7 @@ __device__ void count_start_chunked(const CArgs &A, uint32_t s, const BlockGrp<N
     }
     g.sync();
   }
-  count_finish(A, s, sd, sl, ss, wc, nat, nb, np, g);
+  count_finish(A, s, sd, sl, ss, wc, nat, nb, np, g, mb);
 }
 
 // ---------------------------------------------------------------- kernels
